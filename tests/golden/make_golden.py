@@ -1,0 +1,75 @@
+"""Write the stored oracle values under tests/golden/.
+
+Calls only ``oracle`` (and the seeded input generator).  Usage:
+
+    python tests/golden/make_golden.py c0        # all triplets, seconds
+    python tests/golden/make_golden.py c4        # all triplets, ~1-2 h CPU
+    python tests/golden/make_golden.py c1s       # seeded triplet sample of c1
+
+Each output file holds the configuration, the per-triplet contributions e_t
+(in the oracle's triplet order, or with explicit indices for samples) and the
+per-case sums (math.fsum).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle.triples import CASES, Evaluator, triplets  # noqa: E402
+from paper_2311_10048_gb300.synth import CONFIGS, config_domain  # noqa: E402
+
+SAMPLE_SEED = 20231110
+SAMPLE_PER_CASE = 6
+
+
+def sample_indices(case, na, nb, k=SAMPLE_PER_CASE, seed=SAMPLE_SEED):
+    """Seeded sample of triplet indices of one case (first and last included)."""
+    n = len(triplets(case, na, nb))
+    if n == 0:
+        return []
+    rng = np.random.default_rng(seed + CASES.index(case))
+    pick = set(rng.choice(n, size=min(k, n), replace=False).tolist())
+    pick.update({0, n - 1})
+    return sorted(pick)
+
+
+def run(name):
+    import torch
+    torch.set_num_threads(int(os.environ.get("ORACLE_THREADS", os.cpu_count())))
+    cfg = name[:-1] if name.endswith("s") else name
+    d = config_domain(cfg)
+    na, nb = d["nocc"]
+    ev = Evaluator(d)
+    out = dict(config=cfg, params=CONFIGS[cfg], cases={})
+    t0 = time.time()
+    with torch.no_grad():
+        for case in CASES:
+            trips = triplets(case, na, nb)
+            if name.endswith("s"):
+                idx = sample_indices(case, na, nb)
+                e = [float(ev.triplet_energy(case, trips[q])) for q in idx]
+                out["cases"][case] = dict(index=idx, e=e)
+            else:
+                e = [float(ev.triplet_energy(case, t)) for t in trips]
+                out["cases"][case] = dict(e=e, sum=math.fsum(e))
+            print(name, case, len(e), time.time() - t0, flush=True)
+    if not name.endswith("s"):
+        out["total"] = math.fsum(out["cases"][c]["sum"] for c in CASES)
+    out["oracle_seconds"] = time.time() - t0
+    path = os.path.join(HERE, f"{name}_energy.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=0)
+    print("wrote", path)
+
+
+if __name__ == "__main__":
+    for n in sys.argv[1:]:
+        run(n)
