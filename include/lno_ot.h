@@ -1,0 +1,205 @@
+/*
+ * lno_ot.h -- C ABI of the GB300 (sm_103a) open-shell LNO domain (T) library.
+ *
+ * The library computes the perturbative triples energy E(T) of one local
+ * natural orbital domain (one "local interacting subspace", LIS) from
+ * semicanonical high-spin orbitals: arXiv 2311.10048, Sec. 2.1, eq
+ * cim_pt_energy, evaluated over restricted occupied triplets in the four spin
+ * cases aaa, aab, abb, bbb, with the T1 (disconnected) term:
+ *
+ *   E(T) = sum_cases sum_{restricted ijk} sum_{restricted abc} W (W + V) / D,
+ *   W = t D (connected triples times denominator), V from T1 and <jk||bc>,
+ *   D = e_i + e_j + e_k - e_a - e_b - e_c.
+ *
+ * Restricted ranges: aaa/bbb i<j<k and a<b<c; aab i<j (alpha), K (beta),
+ * a<b (alpha), C (beta); abb I<J (beta), k (alpha), A<B (beta), c (alpha).
+ * The four-index integrals are assembled from density-fitted three-centre
+ * factors, (pq|rs) = sum_Q B^Q_pq B^Q_rs (Sec. 3.2, eqs ed_eri/ed_df_int with
+ * B = I L^-T already applied), one auxiliary index shared by both spins as the
+ * mixed-spin integrals require (Sec. 3.7).
+ *
+ * General conventions
+ *  - Every function returns LNO_OT_OK (0) or a negative lno_ot_status code;
+ *    lno_ot_strerror() names it.  Nothing is thrown and nothing aborts.
+ *  - Domain arrays are DEVICE memory on the context's device, owned by the
+ *    caller, read only (except gradient outputs), never freed by the library.
+ *  - All work is ordered on the context's stream.  The energy calls return
+ *    after the results have reached host memory.
+ *  - Not thread safe per context: one context must not be used by two host
+ *    threads at once.  Different contexts are independent.
+ */
+#ifndef LNO_OT_H
+#define LNO_OT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LNO_OT_API __attribute__((visibility("default")))
+#else
+#define LNO_OT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LNO_OT_OK = 0,
+  LNO_OT_EINVAL = -1,       /* bad sizes, null required pointer, nocc[1] > nocc[0] */
+  LNO_OT_EDEVICE = -2,      /* a pointer is not device memory of the context's device */
+  LNO_OT_ENOMEM = -3,       /* device workspace could not be allocated */
+  LNO_OT_ECUDA = -4,        /* a CUDA runtime/driver call failed */
+  LNO_OT_ETIMEOUT = -5,     /* a bounded device-side wait gave up */
+  LNO_OT_EUNSUPPORTED = -6  /* option or input not supported by this build */
+} lno_ot_status;
+
+/* Arithmetic of the W contractions (Sec. 3.8 (T) step).
+ *  FP64    plain float64 on the CUDA cores for everything (comparator path).
+ *  BF16X3  tensor cores (tcgen05, BF16 inputs, FP32 accumulate): every
+ *          float64 operand is split into 2 BF16 slices with an exact power of
+ *          two scale; 3 slice products per multiply.  FP64 is kept for the
+ *          denominators' orbital energies and the compensated energy sum.
+ *  BF16X6  as BF16X3 with 3 slices per operand and 6 slice products (about
+ *          8 more significant bits per operand).
+ *  TF32    reserved; returns LNO_OT_EUNSUPPORTED in this build. */
+typedef enum {
+  LNO_OT_FP64 = 0,
+  LNO_OT_BF16X3 = 1,
+  LNO_OT_TF32 = 2,
+  LNO_OT_BF16X6 = 3
+} lno_ot_precision;
+
+typedef struct lno_ot_ctx lno_ot_ctx; /* opaque: device, stream, workspace */
+
+typedef struct {
+  int device;             /* CUDA device ordinal */
+  int precision;          /* lno_ot_precision */
+  void* stream;           /* cudaStream_t to order all work on; NULL = the
+                             library creates and owns a non-blocking stream */
+  size_t workspace_bytes; /* upper bound on device workspace; 0 = no bound */
+  const char* tune_cache; /* reserved, may be NULL */
+} lno_ot_options;
+
+/* One domain.  Orbitals of each spin are ordered occupied first (ascending
+ * energy) then virtual; nvir[s] = nbas - nocc[s].  All pointers are device
+ * float64 arrays in C order:
+ *   B[s]    [naux][nbas][nbas]   symmetric in (p,q)
+ *   eps[s]  [nbas]               semicanonical orbital energies (Eh)
+ *   t1[s]   [nocc[s]][nvir[s]]   t^a_i
+ *   t2aa    [na][na][nva][nva]   t^{ab}_{ij}, antisymmetric in (i,j), (a,b)
+ *   t2bb    [nb][nb][nvb][nvb]   t^{AB}_{IJ}
+ *   t2ab    [na][nb][nva][nvb]   t2ab[i][J][a][B] = t^{aB}_{iJ}
+ * High spin: 0 <= nocc[1] <= nocc[0] <= nbas.
+ *
+ * Optional:
+ *   fov[s]        must be NULL (the ROHF f_ov term is not part of this path).
+ *   e_trip[c]     device float64 output, one value per computed triplet of
+ *                 case c (0 aaa, 1 aab, 2 abb, 3 bbb): the triplet's
+ *                 contribution sum_{restricted abc} W (W + V) / D.  NULL = not
+ *                 requested.
+ *   trip_sel[c]   HOST int64 array of n_sel[c] triplet indices (into the
+ *                 lexicographic order of the restricted triplets of case c:
+ *                 aaa (i,j,k), aab (i,j,K), abb (I,J,k), bbb (I,J,K));
+ *                 NULL = all triplets.  Only the selected triplets are
+ *                 computed and summed; e_trip[c][q] belongs to trip_sel[c][q].
+ *   n_sel[c]      length of trip_sel[c] (ignored when it is NULL).        */
+typedef struct {
+  int nbas, naux, nocc[2];
+  const double* B[2];
+  const double* eps[2];
+  const double* t1[2];
+  const double* t2aa;
+  const double* t2bb;
+  const double* t2ab;
+  const double* fov[2];
+  double* e_trip[4];
+  const int64_t* trip_sel[4];
+  int64_t n_sel[4];
+} lno_ot_domain;
+
+/* e = {aaa, aab, abb, bbb, total} in Eh; status as lno_ot_status. */
+typedef struct {
+  double e[5];
+  int status;
+} lno_ot_result;
+
+/* Gradient outputs g = gE * dE/d(input), device float64, caller owned, same
+ * layouts as the inputs, overwritten.  A NULL member skips that gradient.
+ * Gradients of inputs with symmetry are projected onto it: dB symmetric in
+ * (p,q), dt2aa/dt2bb antisymmetric in (i,j) and in (a,b), so that
+ * sum g * delta is the directional derivative for any symmetry-respecting
+ * perturbation delta. */
+typedef struct {
+  double* dB[2];
+  double* deps[2];
+  double* dt1[2];
+  double* dt2aa;
+  double* dt2bb;
+  double* dt2ab;
+} lno_ot_grad;
+
+/* Timings and work counts of the last lno_ot_energy call on a context. */
+typedef struct {
+  double ms_total;          /* call wall time on the stream (CUDA events) */
+  double ms_stage;          /* input checks, layout and DF integral assembly */
+  double ms_contract;       /* W contraction kernels (sum of launches) */
+  double ms_energy;         /* W/V assembly + energy reduction kernels */
+  double flops_algorithmic; /* W contraction flops over the computed triplets,
+                               counting every (b,c) output (full n_v^2) */
+  double flops_executed;    /* method flops the kernels execute (antisymmetric
+                               outputs computed once), one product each */
+  double tensor_flops;      /* tensor-core flops issued incl. slice products */
+  int64_t contract_launches;/* W contraction kernel launches */
+  int64_t energy_launches;  /* energy kernel launches */
+  int64_t other_launches;   /* all other kernel launches */
+  int64_t triplets;         /* triplets computed */
+  int64_t elements;         /* restricted (abc) elements summed */
+} lno_ot_stats;
+
+/* Create a context on opt->device.  *ctx is set only on success. */
+LNO_OT_API int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt);
+
+/* Release the context, its workspace and the stream it created (if any). */
+LNO_OT_API void lno_ot_destroy(lno_ot_ctx* ctx);
+
+/* E(T) of one domain (eq cim_pt_energy, all occupied orbitals of the
+ * domain).  out: host memory; out->status mirrors the return value. */
+LNO_OT_API int lno_ot_energy(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out);
+
+/* E(T) of ndom independent domains (the per-LMO domains of Sec. 3, eq
+ * lno_ccsdpt_energy sums them).  out[d] gets domain d; per-domain status in
+ * out[d].status; returns the first error (or LNO_OT_OK). */
+LNO_OT_API int lno_ot_energy_batched(lno_ot_ctx* ctx, int ndom, const lno_ot_domain* doms,
+                          lno_ot_result* out);
+
+/* Adjoint of lno_ot_energy: g = gE * dE(T)/d(B, eps, T1, T2), W recomputed
+ * per triplet (never stored).  Runs in float64. */
+LNO_OT_API int lno_ot_backward(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE,
+                    lno_ot_grad* g);
+
+/* Stats of the last lno_ot_energy on this context. */
+LNO_OT_API int lno_ot_last_stats(const lno_ot_ctx* ctx, lno_ot_stats* st);
+
+/* Static description of a status code (never NULL). */
+LNO_OT_API const char* lno_ot_strerror(int code);
+
+/* Diagnostic (no counterpart in the paper): the tensor-core contraction
+ * kernel of the W step on one plain product, C[n][m] = sum_k A[m][k] B[n][k]
+ * for device float64 A [M][K], B [N][K], C [N][M] (C written), with S BF16
+ * slices per operand (S = 1..4; the W step uses S = 2 or 3, the DF assembly
+ * S = 4).  Synchronous on `stream` (cudaStream_t, NULL = legacy default).
+ * Returns LNO_OT_EUNSUPPORTED on devices other than sm_103. */
+LNO_OT_API int lno_ot_selftest_gemm(int device, int S, int M, int N, int K, const double* A,
+                                    const double* B, double* C, void* stream);
+
+/* Text of the last CUDA failure seen by this host thread ("" if none). */
+LNO_OT_API const char* lno_ot_last_error(void);
+
+/* Library version string, e.g. "lno_ot 0.1 sm_103a". */
+LNO_OT_API const char* lno_ot_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LNO_OT_H */

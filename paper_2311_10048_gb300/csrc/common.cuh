@@ -1,0 +1,129 @@
+// Internal helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+
+#include "lno_ot.h"
+
+namespace lno {
+
+// Spin-case kinds of one triplet group.
+enum CaseKind { SAME = 0, MIXED = 1 };
+
+// One K-segment of a per-triplet contraction in float64:
+//   XT[n][m] += sign * sum_k A[m][k] * B[n][k],  k < K.
+struct SegF64 {
+  const double* A;  // row m at A + m * lda
+  const double* B;  // row n at B + n * ldb
+  int K;
+  int lda, ldb;
+  double sign;
+};
+
+constexpr int kMaxSeg = 3;
+
+// Problem of a grouped float64 contraction: output XT [N][ldo] (column m < M).
+struct ProbF64 {
+  SegF64 seg[kMaxSeg];
+  int nseg;
+  double* XT;
+};
+
+// Triplet descriptor for the energy kernels.
+struct Trip {
+  int i, j, k;   // same spin: i<j<k; mixed: i<j (spin s), k = K (spin t)
+};
+
+// Energy-kernel arguments of one triplet group.
+struct EnergyArgs {
+  int kind;            // SAME or MIXED
+  int nvs, nvt;        // virtual counts (same spin: nvt == nvs)
+  int nos, not_;       // occupied counts
+  const double* eps_s; // [nbas] orbital energies of spin s (occ then vir)
+  const double* eps_t; // [nbas] spin t
+  const double* t1s;   // [nos][nvs]
+  const double* t1t;   // [not][nvt]
+  // (ia|jb) spin s-s, [nos][nvs][nos][nvs]
+  const double* ovov_ss;
+  // mixed: (jb|KC) as [K][C][j][b] = ovov_ts[K][C][j][b], i.e. [not][nvt][nos][nvs]
+  const double* ovov_ts;
+  const int3* blocks;  // cube tiles (A,B,C) of 16-blocks
+  int nblocks;
+  int pitch_x;         // row pitch (elements) of XT / YT (same: a; mixed: a)
+  int pitch_z;         // row pitch of ZT (mixed: C)
+  int64_t x_stride;    // elements between consecutive triplets' XT (or YT)
+  int64_t z_stride;    // between consecutive ZT
+  const Trip* trips;   // [ntrip]
+  double* partial;     // [ntrip][gridDim.x]
+};
+
+// Tensor-core contraction problem: up to kMaxSeg K-segments, each a row block
+// of a sliced operand tensor addressed through a TMA map (index 0 or 1).
+struct TcSeg {
+  int amap, bmap;   // tensor map index (0/1) for A and B
+  int a_row, b_row; // first row of the A / B operand block in its tensor
+  int K;            // contraction length (k < K is real data)
+  int neg;          // 1: subtract this segment
+};
+
+struct TcProb {
+  TcSeg seg[kMaxSeg];
+  int nseg;
+  int pad_;
+  void* out;        // XT base of this problem (float or double), [N][ldo]
+};
+
+// Operand stores used by the layout kernels.  `part` says whether the value
+// is an amplitude (0) or an integral (1): the two have separate scales.
+struct StoreF64 {
+  double* p;
+  __device__ __forceinline__ void operator()(int64_t idx, double v, int) const { p[idx] = v; }
+};
+
+// Exact BF16 slices: value = scale 2^-7 (s_0 + ... + s_{S-1}), s_0 an integer
+// in [-128,128], s_q a multiple of 2^(-8q) with |s_q| <= 2^(-8q+7), every
+// step rounded to nearest (ties to even) in float64.
+template <int S>
+struct StoreSlices {
+  __nv_bfloat16* p;
+  int64_t slice_stride;  // elements between slices
+  double inv_t;          // 2^7 / amplitude scale
+  double inv_i;          // 2^7 / integral scale
+  __device__ __forceinline__ void operator()(int64_t idx, double v, int part) const {
+    double x = v * (part ? inv_i : inv_t);
+    double w = 1.0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      double q = rint(x * w) / w;   // w = 2^(8s): exact scaling
+      x -= q;                        // exact
+      p[s * slice_stride + idx] = __double2bfloat16(q);
+      w *= 256.0;
+    }
+  }
+};
+
+__host__ __device__ inline int64_t pair_index(int p, int q) {  // p < q
+  return (int64_t)q * (q - 1) / 2 + p;
+}
+__host__ __device__ inline int64_t npairs(int n) { return (int64_t)n * (n - 1) / 2; }
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace lno
+
+#define LNO_CUDA_TRY(expr)                                                   \
+  do {                                                                       \
+    cudaError_t e__ = (expr);                                                \
+    if (e__ != cudaSuccess) {                                                \
+      lno_set_last_error(#expr, e__, __FILE__, __LINE__);                    \
+      return LNO_OT_ECUDA;                                                   \
+    }                                                                        \
+  } while (0)
+
+void lno_set_last_error(const char* what, cudaError_t e, const char* file, int line);

@@ -1,0 +1,658 @@
+// W / V assembly and denominator-weighted energy reduction of one triplet
+// group (eq cim_pt_energy: sum over restricted abc of W (W + V) / D).
+//
+// The contraction kernels leave, per triplet, the P(i/jk)-antisymmetrised
+// intermediate X (same spin) or Y and Z' (mixed spin) in HBM.  This kernel
+// applies the virtual antisymmetriser on the fly:
+//   same spin  W_abc = X[a,(bc)] - X[b,(ac)] + X[c,(ab)]            a<b<c
+//   mixed      W_abC = Y[a,(bC)] - Y[b,(aC)] + Z'[C,(ab)]           a<b
+// adds the T1 term V, and sums W (W + V) / D over the restricted elements.
+//
+// Work split: a CTA owns a list of 16x16x16 cube tiles (A<=B<=C blocks for
+// same spin, A<=B plus any C for mixed) of one triplet, stages the three X
+// sub-cubes it needs in shared memory (each X element is read once), and
+// writes one float64 partial.  Partials are reduced per triplet in a fixed
+// order afterwards, so results are bitwise reproducible.
+//
+// Precision: with float64 X everything is float64.  With float32 X (tensor
+// core path) W, V and W (W+V) are float32, the denominator is formed from
+// float64 orbital energies as a double-float and rounded once to float32,
+// the quotient is correctly rounded, 16 elements are summed in float32 and
+// every such partial is added in float64 (all roundings to nearest, so no
+// systematic bias builds up over the ~1e12 elements of a large domain).
+#include "common.cuh"
+
+namespace lno {
+
+namespace {
+
+constexpr int TB = 16;          // cube tile edge
+constexpr int TP = TB + 1;      // padded row pitch in shared memory
+
+struct TwoF { float hi, lo; };
+
+__device__ __forceinline__ TwoF split_df(double x) {
+  float h = __double2float_rn(x);
+  float l = __double2float_rn(x - (double)h);
+  return {h, l};
+}
+
+// Double-float a - b rounded once to float (Knuth two-sum on the high words).
+__device__ __forceinline__ float df_sub_round(TwoF a, TwoF b) {
+  float s = __fsub_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(-b.hi, bb));
+  float lo = __fadd_rn(err, __fsub_rn(a.lo, b.lo));
+  return __fadd_rn(s, lo);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_row16(T* dst, const T* src) {
+#pragma unroll
+  for (int q = 0; q < TB; ++q) dst[q] = src[q];
+}
+
+template <>
+__device__ __forceinline__ void load_row16<float>(float* dst, const float* src) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float4 v = __ldg(s4 + q);
+    dst[4 * q + 0] = v.x; dst[4 * q + 1] = v.y; dst[4 * q + 2] = v.z; dst[4 * q + 3] = v.w;
+  }
+}
+
+template <>
+__device__ __forceinline__ void load_row16<double>(double* dst, const double* src) {
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    double2 v = __ldg(s2 + q);
+    dst[2 * q + 0] = v.x; dst[2 * q + 1] = v.y;
+  }
+}
+
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(256)
+energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* T1 = reinterpret_cast<T*>(smem_raw);
+  T* T2 = T1 + TB * TB * TP;
+  T* T3 = T2 + TB * TB * TP;
+  // V tables: 9 planes of 16x16 (same: K^{jk},K^{ki},K^{ij} on BC, AC, AB;
+  // mixed: (jb|KC),(ib|KC) on BC; (ja|KC),(ia|KC) on AC; <ij||ab> on AB)
+  __shared__ T vt[9][TB][TP];
+  __shared__ T t1s[9][TB];        // t1 of the triplet's occupied on A, B, C
+  __shared__ double ev[3][TB];    // virtual energies of the A, B, C blocks
+  __shared__ double red[8];
+
+  const int g = blockIdx.y;
+  const Trip tr = a.trips[g];
+  const T* Xg = X + (int64_t)g * a.x_stride;
+  const T* Zg = MIXED ? Z + (int64_t)g * a.z_stride : nullptr;
+  const int tid = threadIdx.x;
+  const int r1 = tid / TB, r2 = tid % TB;
+  const int nvs = a.nvs, nvt = a.nvt;
+  const double eocc = MIXED
+      ? a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_t[tr.k]
+      : a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_s[tr.k];
+
+  double acc = 0.0;
+  for (int q = blockIdx.x; q < a.nblocks; q += gridDim.x) {
+    const int3 blk = a.blocks[q];
+    const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
+    // ---- stage X sub-cubes: thread owns row (r1, r2) of each tile --------
+    if (!MIXED) {
+      {  // T1[b][c][a] = X[a,(bc)]
+        int b = b0 + r1, c = c0 + r2;
+        if (b < c && c < nvs)
+          load_row16(T1 + (r1 * TB + r2) * TP, Xg + pair_index(b, c) * a.pitch_x + a0);
+      }
+      {  // T2[a][c][b] = X[b,(ac)]
+        int aa = a0 + r1, c = c0 + r2;
+        if (aa < c && c < nvs)
+          load_row16(T2 + (r1 * TB + r2) * TP, Xg + pair_index(aa, c) * a.pitch_x + b0);
+      }
+      {  // T3[a][b][c] = X[c,(ab)]
+        int aa = a0 + r1, b = b0 + r2;
+        if (aa < b && b < nvs)
+          load_row16(T3 + (r1 * TB + r2) * TP, Xg + pair_index(aa, b) * a.pitch_x + c0);
+      }
+    } else {
+      {  // T1[b][C][a] = Y[a,(bC)]
+        int b = b0 + r1, c = c0 + r2;
+        if (b < nvs && c < nvt)
+          load_row16(T1 + (r1 * TB + r2) * TP, Xg + ((int64_t)b * nvt + c) * a.pitch_x + a0);
+      }
+      {  // T2[a][C][b] = Y[b,(aC)]
+        int aa = a0 + r1, c = c0 + r2;
+        if (aa < nvs && c < nvt)
+          load_row16(T2 + (r1 * TB + r2) * TP, Xg + ((int64_t)aa * nvt + c) * a.pitch_x + b0);
+      }
+      {  // T3[a][b][C] = Z'[C,(ab)]
+        int aa = a0 + r1, b = b0 + r2;
+        if (aa < b && b < nvs)
+          load_row16(T3 + (r1 * TB + r2) * TP, Zg + pair_index(aa, b) * a.pitch_z + c0);
+      }
+    }
+    // ---- V tables -----------------------------------------------------------
+    {
+      const int nos = a.nos;
+      if (!MIXED) {
+        const int occ3[3][2] = {{tr.j, tr.k}, {tr.k, tr.i}, {tr.i, tr.j}};
+        const int offs[3][2] = {{b0, c0}, {a0, c0}, {a0, b0}};
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {          // index plane (BC, AC, AB)
+          const int x = offs[pl][0] + r1, y = offs[pl][1] + r2;
+#pragma unroll
+          for (int o = 0; o < 3; ++o) {
+            T v = 0;
+            if (x < nvs && y < nvs) {
+              const int p = occ3[o][0], r = occ3[o][1];
+              // K^{pr}_{xy} = (px|ry) - (py|rx)
+              const double* ov = a.ovov_ss;
+              double v1 = ov[(((int64_t)p * nvs + x) * nos + r) * nvs + y];
+              double v2 = ov[(((int64_t)p * nvs + y) * nos + r) * nvs + x];
+              v = (T)(v1 - v2);
+            }
+            vt[pl * 3 + o][r1][r2] = v;
+          }
+        }
+      } else {
+        const int nt = a.not_;
+        const int K = tr.k;
+        // planes 0,1: (jb|KC),(ib|KC) on (B,C); 2,3: (ja|KC),(ia|KC) on (A,C)
+        const int offs[2] = {b0, a0};
+#pragma unroll
+        for (int pl = 0; pl < 2; ++pl) {
+          const int x = offs[pl] + r1, y = c0 + r2;
+#pragma unroll
+          for (int o = 0; o < 2; ++o) {
+            T v = 0;
+            if (x < nvs && y < nvt) {
+              const int p = o == 0 ? tr.j : tr.i;
+              v = (T)a.ovov_ts[(((int64_t)K * nvt + y) * nos + p) * nvs + x];
+            }
+            vt[pl * 2 + o][r1][r2] = v;
+          }
+        }
+        {  // plane 4: (ia|jb) - (ib|ja) on (A,B)
+          const int x = a0 + r1, y = b0 + r2;
+          T v = 0;
+          if (x < nvs && y < nvs) {
+            const double* ov = a.ovov_ss;
+            double v1 = ov[(((int64_t)tr.i * nvs + x) * nos + tr.j) * nvs + y];
+            double v2 = ov[(((int64_t)tr.i * nvs + y) * nos + tr.j) * nvs + x];
+            v = (T)(v1 - v2);
+          }
+          vt[4][r1][r2] = v;
+        }
+        (void)nt;
+      }
+      if (tid < 3 * TB) {
+        const int bl = tid / TB, l = tid % TB;
+        const int base = bl == 0 ? a0 : (bl == 1 ? b0 : c0);
+        const int x = base + l;
+        const bool tblock = MIXED && bl == 2;
+        const int nv = tblock ? nvt : nvs;
+        if (!MIXED) {
+          const int occ[3] = {tr.i, tr.j, tr.k};
+#pragma unroll
+          for (int o = 0; o < 3; ++o)
+            t1s[bl * 3 + o][l] = x < nvs ? (T)a.t1s[(int64_t)occ[o] * nvs + x] : (T)0;
+        } else if (!tblock) {
+          t1s[bl * 3 + 0][l] = x < nvs ? (T)a.t1s[(int64_t)tr.i * nvs + x] : (T)0;
+          t1s[bl * 3 + 1][l] = x < nvs ? (T)a.t1s[(int64_t)tr.j * nvs + x] : (T)0;
+        } else {
+          t1s[bl * 3 + 0][l] = x < nvt ? (T)a.t1t[(int64_t)tr.k * nvt + x] : (T)0;
+        }
+        const double* e = tblock ? a.eps_t : a.eps_s;
+        const int no = tblock ? a.not_ : a.nos;
+        ev[bl][l] = x < nv ? e[no + x] : 0.0;
+      }
+    }
+    __syncthreads();
+    // ---- elements: thread (b = r1, c = r2), loop over a ---------------------
+    {
+      const int bl = r1, cl = r2;
+      const int b = b0 + bl, c = c0 + cl;
+      const bool rowok = MIXED ? (b < nvs && c < nvt) : (b < c && c < nvs);
+      if (rowok) {
+        const double dbc = eocc - ev[1][bl] - ev[2][cl];
+        int amax = MIXED ? min(b, a0 + TB) : min(b, a0 + TB);  // a < b
+        const int na = amax - a0;
+        if constexpr (sizeof(T) == 8) {
+          for (int al = 0; al < na; ++al) {
+            const double x1 = T1[(bl * TB + cl) * TP + al];
+            const double x2 = T2[(al * TB + cl) * TP + bl];
+            const double x3 = T3[(al * TB + bl) * TP + cl];
+            const double w = x1 - x2 + x3;
+            double v;
+            if (!MIXED) {
+              const double ya = t1s[0][al] * vt[0][bl][cl] + t1s[1][al] * vt[1][bl][cl] +
+                                t1s[2][al] * vt[2][bl][cl];
+              const double yb = t1s[3][bl] * vt[3][al][cl] + t1s[4][bl] * vt[4][al][cl] +
+                                t1s[5][bl] * vt[5][al][cl];
+              const double yc = t1s[6][cl] * vt[6][al][bl] + t1s[7][cl] * vt[7][al][bl] +
+                                t1s[8][cl] * vt[8][al][bl];
+              v = ya - yb + yc;
+            } else {
+              v = t1s[0][al] * vt[0][bl][cl] - t1s[1][al] * vt[1][bl][cl] -
+                  t1s[3][bl] * vt[2][al][cl] + t1s[4][bl] * vt[3][al][cl] +
+                  t1s[6][cl] * vt[4][al][bl];
+            }
+            const double D = dbc - ev[0][al];
+            acc += w * (w + v) / D;
+          }
+        } else {
+          const TwoF dd = split_df(dbc);
+          float part = 0.f;
+          for (int al = 0; al < na; ++al) {
+            const float x1 = T1[(bl * TB + cl) * TP + al];
+            const float x2 = T2[(al * TB + cl) * TP + bl];
+            const float x3 = T3[(al * TB + bl) * TP + cl];
+            const float w = x1 - x2 + x3;
+            float v;
+            if (!MIXED) {
+              const float ya = t1s[0][al] * vt[0][bl][cl] + t1s[1][al] * vt[1][bl][cl] +
+                               t1s[2][al] * vt[2][bl][cl];
+              const float yb = t1s[3][bl] * vt[3][al][cl] + t1s[4][bl] * vt[4][al][cl] +
+                               t1s[5][bl] * vt[5][al][cl];
+              const float yc = t1s[6][cl] * vt[6][al][bl] + t1s[7][cl] * vt[7][al][bl] +
+                               t1s[8][cl] * vt[8][al][bl];
+              v = ya - yb + yc;
+            } else {
+              v = t1s[0][al] * vt[0][bl][cl] - t1s[1][al] * vt[1][bl][cl] -
+                  t1s[3][bl] * vt[2][al][cl] + t1s[4][bl] * vt[3][al][cl] +
+                  t1s[6][cl] * vt[4][al][bl];
+            }
+            const float num = __fmul_rn(w, __fadd_rn(w, v));
+            const float D = df_sub_round(dd, split_df(ev[0][al]));
+            part = __fadd_rn(part, __fdiv_rn(num, D));
+          }
+          acc += (double)part;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // ---- CTA reduction (fixed order) ---------------------------------------------
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    a.partial[(int64_t)g * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core path (float32 X): per-triplet V tables, then the energy.
+//
+// energy_prep writes, per triplet of the group, the float32 integral tables
+// the T1 term needs (full square, rows padded to a multiple of 16):
+//   same spin: plane o = K^{pr}_{xy} = (px|ry) - (py|rx) for
+//              (p,r) = (j,k), (k,i), (i,j)                  [3][nv][pv]
+//   mixed:     plane 0 (jx|KC), plane 1 (ix|KC)             [nvs][pvt] each
+//              plane 2 (ia|jb) - (ib|ja)                    [nvs][pvs]
+__global__ void energy_prep(EnergyArgs a, float* __restrict__ vt_out, int64_t vt_stride, int pv,
+                            int pvt) {
+  const int g = blockIdx.y;
+  const Trip tr = a.trips[g];
+  float* out = vt_out + (int64_t)g * vt_stride;
+  const int nvs = a.nvs, nvt = a.nvt, nos = a.nos;
+  if (a.kind == SAME) {
+    const int occ3[3][2] = {{tr.j, tr.k}, {tr.k, tr.i}, {tr.i, tr.j}};
+    const int64_t n = 3LL * nvs * nvs;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+      const int y = (int)(idx % nvs);
+      const int64_t r = idx / nvs;
+      const int x = (int)(r % nvs);
+      const int o = (int)(r / nvs);
+      const int p = occ3[o][0], q = occ3[o][1];
+      const double* ov = a.ovov_ss;
+      const double v1 = ov[(((int64_t)p * nvs + x) * nos + q) * nvs + y];
+      const double v2 = ov[(((int64_t)p * nvs + y) * nos + q) * nvs + x];
+      out[((int64_t)o * nvs + x) * pv + y] = (float)(v1 - v2);
+    }
+  } else {
+    const int64_t n1 = 2LL * nvs * nvt, n2 = (int64_t)nvs * nvs;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n1 + n2;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+      if (idx < n1) {
+        const int C = (int)(idx % nvt);
+        const int64_t r = idx / nvt;
+        const int x = (int)(r % nvs);
+        const int o = (int)(r / nvs);   // 0: j, 1: i
+        const int p = o == 0 ? tr.j : tr.i;
+        out[((int64_t)o * nvs + x) * pvt + C] =
+            (float)a.ovov_ts[(((int64_t)tr.k * nvt + C) * nos + p) * nvs + x];
+      } else {
+        const int64_t q = idx - n1;
+        const int y = (int)(q % nvs), x = (int)(q / nvs);
+        const double* ov = a.ovov_ss;
+        const double v1 = ov[(((int64_t)tr.i * nvs + x) * nos + tr.j) * nvs + y];
+        const double v2 = ov[(((int64_t)tr.i * nvs + y) * nos + tr.j) * nvs + x];
+        out[2LL * nvs * pvt + (int64_t)x * pv + y] = (float)(v1 - v2);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// double-float a - b (both hi+lo), renormalised
+__device__ __forceinline__ TwoF df_sub(TwoF a, TwoF b) {
+  float s, e;
+  two_sum(a.hi, -b.hi, s, e);
+  e = __fadd_rn(e, __fsub_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+// Energy of float32 X with register prefetch of the next cube tile.
+template <bool MIXED>
+__global__ void __launch_bounds__(256, 2)
+energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ Z,
+           const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt) {
+  __shared__ float T1[TB * TB * TP], T2[TB * TB * TP], T3[TB * TB * TP];
+  __shared__ float vt[9][TB][TP];
+  __shared__ float t1s[9][TB];
+  __shared__ float eh[3][TB], el[3][TB];
+  __shared__ double red[8];
+
+  const int g = blockIdx.y;
+  const Trip tr = a.trips[g];
+  const float* Xg = X + (int64_t)g * a.x_stride;
+  const float* Zg = MIXED ? Z + (int64_t)g * a.z_stride : nullptr;
+  const float* Vg = VT + (int64_t)g * vt_stride;
+  const int tid = threadIdx.x;
+  const int r1 = tid / TB, r2 = tid % TB;
+  const int nvs = a.nvs, nvt = a.nvt;
+  const TwoF eocc = split_df(MIXED ? a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_t[tr.k]
+                                   : a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_s[tr.k]);
+
+  float4 xr[3][4];
+  float vr[9];
+  float t1r[3];
+  TwoF er;
+  bool ok1 = false, ok2 = false, ok3 = false;
+
+  auto fetch = [&](int q) {
+    const int3 blk = a.blocks[q];
+    const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
+    const float4* p1 = nullptr;
+    const float4* p2 = nullptr;
+    const float4* p3 = nullptr;
+    if (!MIXED) {
+      int b = b0 + r1, c = c0 + r2;
+      ok1 = b < c && c < nvs;
+      if (ok1) p1 = reinterpret_cast<const float4*>(Xg + pair_index(b, c) * a.pitch_x + a0);
+      int aa = a0 + r1;
+      ok2 = aa < c && c < nvs;
+      if (ok2) p2 = reinterpret_cast<const float4*>(Xg + pair_index(aa, c) * a.pitch_x + b0);
+      b = b0 + r2;
+      ok3 = aa < b && b < nvs;
+      if (ok3) p3 = reinterpret_cast<const float4*>(Xg + pair_index(aa, b) * a.pitch_x + c0);
+    } else {
+      int b = b0 + r1, c = c0 + r2;
+      ok1 = b < nvs && c < nvt;
+      if (ok1) p1 = reinterpret_cast<const float4*>(Xg + ((int64_t)b * nvt + c) * a.pitch_x + a0);
+      int aa = a0 + r1;
+      ok2 = aa < nvs && c < nvt;
+      if (ok2) p2 = reinterpret_cast<const float4*>(Xg + ((int64_t)aa * nvt + c) * a.pitch_x + b0);
+      b = b0 + r2;
+      ok3 = aa < b && b < nvs;
+      if (ok3) p3 = reinterpret_cast<const float4*>(Zg + pair_index(aa, b) * a.pitch_z + c0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (ok1) xr[0][u] = __ldg(p1 + u);
+      if (ok2) xr[1][u] = __ldg(p2 + u);
+      if (ok3) xr[2][u] = __ldg(p3 + u);
+    }
+    // V tables: plane element (r1, r2)
+    if (!MIXED) {
+      const int rows[3] = {b0, a0, a0}, cols[3] = {c0, c0, b0};
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl) {
+        const int x = rows[pl] + r1, y = cols[pl] + r2;
+        const bool in = x < nvs && y < nvs;
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+          vr[pl * 3 + o] = in ? __ldg(Vg + ((int64_t)o * nvs + x) * pv + y) : 0.f;
+      }
+    } else {
+      const int rows[2] = {b0, a0};
+#pragma unroll
+      for (int pl = 0; pl < 2; ++pl) {
+        const int x = rows[pl] + r1, y = c0 + r2;
+        const bool in = x < nvs && y < nvt;
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+          vr[pl * 2 + o] = in ? __ldg(Vg + ((int64_t)o * nvs + x) * pvt + y) : 0.f;
+      }
+      const int x = a0 + r1, y = b0 + r2;
+      vr[4] = (x < nvs && y < nvs) ? __ldg(Vg + 2LL * nvs * pvt + (int64_t)x * pv + y) : 0.f;
+    }
+    if (tid < 3 * TB) {
+      const int bl = tid / TB, l = tid % TB;
+      const int base = bl == 0 ? a0 : (bl == 1 ? b0 : c0);
+      const int x = base + l;
+      const bool tblock = MIXED && bl == 2;
+      const int nv = tblock ? nvt : nvs;
+      if (!MIXED) {
+        const int occ[3] = {tr.i, tr.j, tr.k};
+#pragma unroll
+        for (int o = 0; o < 3; ++o) t1r[o] = x < nvs ? (float)a.t1s[(int64_t)occ[o] * nvs + x] : 0.f;
+      } else if (!tblock) {
+        t1r[0] = x < nvs ? (float)a.t1s[(int64_t)tr.i * nvs + x] : 0.f;
+        t1r[1] = x < nvs ? (float)a.t1s[(int64_t)tr.j * nvs + x] : 0.f;
+        t1r[2] = 0.f;
+      } else {
+        t1r[0] = x < nvt ? (float)a.t1t[(int64_t)tr.k * nvt + x] : 0.f;
+        t1r[1] = t1r[2] = 0.f;
+      }
+      const double* e = tblock ? a.eps_t : a.eps_s;
+      const int no = tblock ? a.not_ : a.nos;
+      er = split_df(x < nv ? e[no + x] : 0.0);
+    }
+  };
+
+  TwoF acc = {0.f, 0.f};
+  int q = blockIdx.x;
+  if (q < a.nblocks) fetch(q);
+  for (; q < a.nblocks; q += gridDim.x) {
+    const int3 blk = a.blocks[q];
+    const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
+    // ---- registers -> shared ----
+    {
+      float* d1 = T1 + (r1 * TB + r2) * TP;
+      float* d2 = T2 + (r1 * TB + r2) * TP;
+      float* d3 = T3 + (r1 * TB + r2) * TP;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (ok1) { d1[4 * u] = xr[0][u].x; d1[4 * u + 1] = xr[0][u].y; d1[4 * u + 2] = xr[0][u].z; d1[4 * u + 3] = xr[0][u].w; }
+        if (ok2) { d2[4 * u] = xr[1][u].x; d2[4 * u + 1] = xr[1][u].y; d2[4 * u + 2] = xr[1][u].z; d2[4 * u + 3] = xr[1][u].w; }
+        if (ok3) { d3[4 * u] = xr[2][u].x; d3[4 * u + 1] = xr[2][u].y; d3[4 * u + 2] = xr[2][u].z; d3[4 * u + 3] = xr[2][u].w; }
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+        if (!MIXED || k < 5) vt[k][r1][r2] = vr[k];
+      if (tid < 3 * TB) {
+        const int bl = tid / TB, l = tid % TB;
+        t1s[bl * 3 + 0][l] = t1r[0];
+        t1s[bl * 3 + 1][l] = t1r[1];
+        t1s[bl * 3 + 2][l] = t1r[2];
+        eh[bl][l] = er.hi;
+        el[bl][l] = er.lo;
+      }
+    }
+    __syncthreads();
+    if (q + (int)gridDim.x < a.nblocks) fetch(q + gridDim.x);  // next tile in flight
+    // ---- elements: thread (b = r1, c = r2), loop over a ----
+    {
+      const int bl = r1, cl = r2;
+      const int b = b0 + bl, c = c0 + cl;
+      const bool rowok = MIXED ? (b < nvs && c < nvt) : (b < c && c < nvs);
+      if (rowok) {
+        const TwoF dbc = df_sub(df_sub(eocc, TwoF{eh[1][bl], el[1][bl]}), TwoF{eh[2][cl], el[2][cl]});
+        const int na = min(b, a0 + TB) - a0;
+        const float* x1p = T1 + (bl * TB + cl) * TP;
+        float part = 0.f;
+        if (!MIXED) {
+          const float k0 = vt[0][bl][cl], k1 = vt[1][bl][cl], k2 = vt[2][bl][cl];
+          const float tb0 = t1s[3][bl], tb1 = t1s[4][bl], tb2 = t1s[5][bl];
+          const float tc0 = t1s[6][cl], tc1 = t1s[7][cl], tc2 = t1s[8][cl];
+          for (int al = 0; al < na; ++al) {
+            const float w = x1p[al] - T2[(al * TB + cl) * TP + bl] + T3[(al * TB + bl) * TP + cl];
+            const float ya = t1s[0][al] * k0 + t1s[1][al] * k1 + t1s[2][al] * k2;
+            const float yb = tb0 * vt[3][al][cl] + tb1 * vt[4][al][cl] + tb2 * vt[5][al][cl];
+            const float yc = tc0 * vt[6][al][bl] + tc1 * vt[7][al][bl] + tc2 * vt[8][al][bl];
+            const float v = ya - yb + yc;
+            const float num = __fmul_rn(w, __fadd_rn(w, v));
+            float s, e;
+            two_sum(dbc.hi, -eh[0][al], s, e);
+            const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc.lo, el[0][al])));
+            part = __fadd_rn(part, __fdiv_rn(num, D));
+          }
+        } else {
+          const float mjb = vt[0][bl][cl], mib = vt[1][bl][cl];
+          const float tbi = t1s[3][bl], tbj = t1s[4][bl], tC = t1s[6][cl];
+          for (int al = 0; al < na; ++al) {
+            const float w = x1p[al] - T2[(al * TB + cl) * TP + bl] + T3[(al * TB + bl) * TP + cl];
+            const float v = t1s[0][al] * mjb - t1s[1][al] * mib - tbi * vt[2][al][cl] +
+                            tbj * vt[3][al][cl] + tC * vt[4][al][bl];
+            const float num = __fmul_rn(w, __fadd_rn(w, v));
+            float s, e;
+            two_sum(dbc.hi, -eh[0][al], s, e);
+            const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc.lo, el[0][al])));
+            part = __fadd_rn(part, __fdiv_rn(num, D));
+          }
+        }
+        float s, e;
+        two_sum(acc.hi, part, s, e);
+        acc = {s, __fadd_rn(acc.lo, e)};
+      }
+    }
+    __syncthreads();
+  }
+  double dacc = (double)acc.hi + (double)acc.lo;
+  for (int off = 16; off > 0; off >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, off);
+  if ((tid & 31) == 0) red[tid >> 5] = dacc;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < 8; ++w) sum += red[w];
+    a.partial[(int64_t)g * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+// e_trip[g] = sum_p partial[g][p] (Neumaier), one thread per triplet.
+__global__ void reduce_partials(const double* __restrict__ partial, int np, int ntrip,
+                                double* __restrict__ e_trip) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ntrip) return;
+  double s = 0.0, c = 0.0;
+  for (int p = 0; p < np; ++p) {
+    double x = partial[(int64_t)g * np + p];
+    double t = s + x;
+    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  e_trip[g] = s + c;
+}
+
+// out[0] = Neumaier sum of e[0..n): one CTA of 256 threads, fixed order.
+__global__ void neumaier_sum(const double* __restrict__ e, int64_t n, double* out) {
+  __shared__ double ss[256], cc[256];
+  double s = 0.0, c = 0.0;
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
+    double x = e[q];
+    double t = s + x;
+    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  ss[threadIdx.x] = s;
+  cc[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, C = 0.0;
+    for (int q = 0; q < (int)blockDim.x; ++q) {
+      double x = ss[q];
+      double t = S + x;
+      C += fabs(S) >= fabs(x) ? (S - t) + x : (x - t) + S;
+      S = t;
+      C += cc[q];
+    }
+    out[0] = S + C;
+  }
+}
+
+}  // namespace
+
+size_t energy_smem_bytes(bool f64) { return 3 * TB * TB * TP * (f64 ? 8 : 4); }
+
+// float32-X path: V-table prep + energy (grid: nchunks x ntrip).
+cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* Z, float* vtab,
+                              int64_t vt_stride, int pv, int pvt, int ntrip, int nchunks,
+                              cudaStream_t st) {
+  if (ntrip <= 0) return cudaSuccess;
+  dim3 gp(64, ntrip);
+  energy_prep<<<gp, 256, 0, st>>>(a, vtab, vt_stride, pv, pvt);
+  dim3 grid(nchunks, ntrip);
+  if (a.kind == SAME)
+    energy_f32<false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+  else
+    energy_f32<true><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const EnergyArgs& a, const void* X, const void* Z, bool f64,
+                          int ntrip, int nchunks, cudaStream_t st) {
+  if (ntrip <= 0) return cudaSuccess;
+  dim3 grid(nchunks, ntrip);
+  const size_t sm = energy_smem_bytes(f64);
+  if (f64) {
+    if (a.kind == SAME) {
+      auto k = energy_group<double, false>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k<<<grid, 256, sm, st>>>(a, (const double*)X, (const double*)Z);
+    } else {
+      auto k = energy_group<double, true>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k<<<grid, 256, sm, st>>>(a, (const double*)X, (const double*)Z);
+    }
+  } else {
+    if (a.kind == SAME) {
+      auto k = energy_group<float, false>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k<<<grid, 256, sm, st>>>(a, (const float*)X, (const float*)Z);
+    } else {
+      auto k = energy_group<float, true>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k<<<grid, 256, sm, st>>>(a, (const float*)X, (const float*)Z);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double* partial, int np, int ntrip, double* e_trip,
+                                   cudaStream_t st) {
+  if (ntrip <= 0) return cudaSuccess;
+  reduce_partials<<<ceil_div(ntrip, 128), 128, 0, st>>>(partial, np, ntrip, e_trip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_neumaier_sum(const double* e, int64_t n, double* out, cudaStream_t st) {
+  neumaier_sum<<<1, 256, 0, st>>>(e, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lno

@@ -1,0 +1,1189 @@
+// Host driver of the C ABI declared in include/lno_ot.h.
+//
+// One domain (eq cim_pt_energy, spin cases aaa, aab, abb, bbb):
+//  1. stage: validate, lay the DF factors out as K-contiguous blocks
+//     (occ-occ, occ-vir, vir-vir rows, Q fastest), assemble (ia|jb);
+//  2. per spin s: assemble the DF integrals and build the K-concatenated
+//     contraction operands AT, BT (same spin) and A1, BG, BF, AT2 (mixed,
+//     spin s twice and the other spin once), see pack.cu;
+//  3. per group of triplets: one grouped contraction launch writes X (same
+//     spin) or Y and Z' (mixed) per triplet, one energy launch assembles W,
+//     V and sums W (W + V) / D per triplet (energy.cu);
+//  4. per-triplet sums -> per-case compensated sums -> host.
+// Precision FP64 runs every contraction on the CUDA cores in float64; the
+// BF16X3 / BF16X6 precisions run them on the tensor cores on exact BF16
+// slices (tc_gemm.cu), with float64 kept for orbital energies and sums.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lno {
+// gemm_f64.cu
+cudaError_t launch_gemm_f64(const ProbF64* probs_dev, int nprob, int M, int N, int ldo,
+                            cudaStream_t st);
+// energy.cu
+cudaError_t launch_energy(const EnergyArgs& a, const void* X, const void* Z, bool f64, int ntrip,
+                          int nchunks, cudaStream_t st);
+cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* Z, float* vtab,
+                              int64_t vt_stride, int pv, int pvt, int ntrip, int nchunks,
+                              cudaStream_t st);
+cudaError_t launch_reduce_partials(const double* partial, int np, int ntrip, double* e_trip,
+                                   cudaStream_t st);
+cudaError_t launch_neumaier_sum(const double* e, int64_t n, double* out, cudaStream_t st);
+// pack.cu
+template <class St>
+cudaError_t launch_transpose_block(const double*, int, int, int, int, int, int, int, St,
+                                   cudaStream_t);
+template <class St>
+cudaError_t launch_pack_at_same(const int2*, int, int, int, int, const double*, const double*, St,
+                                cudaStream_t);
+template <class St>
+cudaError_t launch_pack_bt_same(int, int, int, int, int, const double*, const double*, St,
+                                cudaStream_t);
+template <class St>
+cudaError_t launch_pack_a1(const int2*, int, int, int, int, int, int, const double*,
+                           const double*, St, cudaStream_t);
+template <class St>
+cudaError_t launch_pack_bg(int, int, int, int, int, int, int, const double*, const double*, St,
+                           cudaStream_t);
+template <class St>
+cudaError_t launch_pack_bf(int, int, int, int, int, int, int, const double*, const double*, St,
+                           cudaStream_t);
+template <class St>
+cudaError_t launch_pack_at2(const int2*, int, int, int, int, int, int, const double*,
+                            const double*, St, cudaStream_t);
+cudaError_t launch_transpose_t2ab(const double*, int, int, int, int, double*, cudaStream_t);
+cudaError_t launch_absmax(const double*, int64_t, unsigned long long*, cudaStream_t);
+// tc_gemm.cu
+int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
+                     int64_t slice_stride, int box_rows);
+template <int S, int BN, typename OutT>
+cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
+                           int nprob, int M, int N, int ldo, double scale, int* flag,
+                           unsigned long long* amax, int nsm, cudaStream_t st);
+}  // namespace lno
+
+using namespace lno;
+
+// ----------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+void lno_set_last_error(const char* what, cudaError_t e, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_last_error = buf;
+}
+
+struct lno_ot_ctx {
+  int device = 0;
+  int prec = LNO_OT_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t ws_limit = 0;
+  int nsm = 152;
+  int* d_flag = nullptr;               // device error flag (bounded waits)
+  unsigned long long* d_amax = nullptr;
+  double* d_sums = nullptr;            // [8]
+  lno_ot_stats stats{};
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+#define TRY(expr)                       \
+  do {                                  \
+    int rc__ = (expr);                  \
+    if (rc__ != LNO_OT_OK) return rc__; \
+  } while (0)
+
+// Stream-ordered device allocations released at scope exit.
+struct Arena {
+  cudaStream_t st;
+  size_t limit, used = 0;
+  std::vector<void*> ptrs;
+  Arena(cudaStream_t s, size_t lim) : st(s), limit(lim) {}
+  ~Arena() { release(); }
+  void release() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+    ptrs.clear();
+    used = 0;
+  }
+  template <typename T>
+  int get(T** out, size_t n) {
+    size_t bytes = std::max<size_t>(n * sizeof(T), 256);
+    bytes = (bytes + 255) / 256 * 256;
+    if (limit && used + bytes > limit) return LNO_OT_ENOMEM;
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return LNO_OT_ENOMEM;
+    }
+    ptrs.push_back(p);
+    used += bytes;
+    *out = static_cast<T*>(p);
+    return LNO_OT_OK;
+  }
+  void drop(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFreeAsync(q, st);
+        q = ptrs.back();
+        ptrs.pop_back();
+        return;
+      }
+  }
+};
+
+int cuda_rc(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LNO_OT_OK;
+  lno_set_last_error(what, e, __FILE__, __LINE__);
+  cudaGetLastError();
+  return LNO_OT_ECUDA;
+}
+#define CU(...) TRY(cuda_rc((__VA_ARGS__), #__VA_ARGS__))
+
+int64_t pow2ceil_exp(double x) {  // smallest e with 2^e >= x (x > 0)
+  int e;
+  double m = std::frexp(x, &e);    // x = m 2^e, m in [0.5, 1)
+  return (m == 0.5) ? e - 1 : e;
+}
+
+double pow2_scale(double amax) {
+  if (!(amax > 0.0) || !std::isfinite(amax)) return 1.0;
+  return std::ldexp(1.0, (int)pow2ceil_exp(amax));
+}
+
+// K-concatenated operand tensor: nslot slots of `rows` rows, pitch Kp.
+struct Operand {
+  int nslot = 0;
+  int64_t rows = 0;  // rows per slot
+  int K = 0, Kp = 0;
+  double* f64 = nullptr;
+  __nv_bfloat16* bf = nullptr;
+  int S = 0;
+  int64_t slice_stride = 0;
+  CUtensorMap mapA, mapB, mapB128;  // box rows: 128 (A role), 256 / 128 (B role)
+  int64_t total_rows() const { return (int64_t)nslot * rows; }
+};
+
+struct Run {
+  lno_ot_ctx* ctx;
+  const lno_ot_domain* dom;
+  cudaStream_t st;
+  Arena arena;
+  bool f64;
+  int S = 0;          // slices of the W contraction operands
+  int Sdf = 4;        // slices of the DF factors
+  double sigT = 1, sigI = 1, sigB = 1;
+  bool amax_pass = false;  // true while measuring integral magnitudes
+  double amax_int = 0.0;
+  int nbas, naux, no[2], nv[2];
+  // DF factor blocks per spin (rows, K = naux)
+  Operand Boo[2], Bov[2], Bvv[2];
+  double* ovov_ss[2] = {nullptr, nullptr};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> contract_ev, energy_ev;
+  lno_ot_stats* stats;
+
+  Run(lno_ot_ctx* c, const lno_ot_domain* d)
+      : ctx(c), dom(d), st(c->stream), arena(c->stream, c->ws_limit), stats(&c->stats) {}
+
+  cudaEvent_t event() {
+    if (ctx->ev_used == ctx->ev_pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      ctx->ev_pool.push_back(e);
+    }
+    return ctx->ev_pool[ctx->ev_used++];
+  }
+
+  // ---- operand allocation -------------------------------------------------
+  int alloc_operand(Operand& op, int nslot, int64_t rows, int K, int S_) {
+    return alloc_operand(arena, op, nslot, rows, K, S_);
+  }
+  int alloc_operand(Arena& ar, Operand& op, int nslot, int64_t rows, int K, int S_) {
+    op.nslot = nslot;
+    op.rows = rows;
+    op.K = K;
+    op.Kp = (int)round_up(std::max(K, 1), 8);
+    op.S = f64 ? 0 : S_;
+    const int64_t n = std::max<int64_t>((int64_t)nslot * rows * op.Kp, 8);
+    if (f64) {
+      TRY(ar.get(&op.f64, (size_t)n));
+    } else {
+      op.slice_stride = round_up(n, 8);
+      TRY(ar.get(&op.bf, (size_t)(op.slice_stride * op.S)));
+      TRY(make_operand_map(&op.mapA, op.bf, op.Kp, std::max<int64_t>(op.total_rows(), 1), op.S,
+                           op.slice_stride, 128));
+      TRY(make_operand_map(&op.mapB, op.bf, op.Kp, std::max<int64_t>(op.total_rows(), 1), op.S,
+                           op.slice_stride, 256));
+      TRY(make_operand_map(&op.mapB128, op.bf, op.Kp, std::max<int64_t>(op.total_rows(), 1),
+                           op.S, op.slice_stride, 128));
+    }
+    return LNO_OT_OK;
+  }
+
+  // Store functor for an operand (amplitude scale sigT, integral scale sigI).
+  template <int SS>
+  StoreSlices<SS> slices(const Operand& op) const {
+    return StoreSlices<SS>{op.bf, op.slice_stride, 128.0 / sigT, 128.0 / sigI};
+  }
+
+  // ---- DF integrals: out[n][m] = sum_Q L[m][Q] R[n][Q] (float64) ------------
+  // L rows [l0, l0+M) of operand Lo, R rows [r0, r0+N) of Ro.
+  int df(const Operand& Lo, int64_t l0, int M, const Operand& Ro, int64_t r0, int N, double* out,
+         int ldo) {
+    if (M <= 0 || N <= 0) return LNO_OT_OK;
+    stats->other_launches++;
+    if (f64) {
+      ProbF64 p{};
+      p.nseg = 1;
+      p.seg[0] = SegF64{Lo.f64 + l0 * Lo.Kp, Ro.f64 + r0 * Ro.Kp, naux, Lo.Kp, Ro.Kp, 1.0};
+      p.XT = out;
+      ProbF64* dp;
+      TRY(arena.get(&dp, 1));
+      CU(cudaMemcpyAsync(dp, &p, sizeof p, cudaMemcpyHostToDevice, st));
+      CU(launch_gemm_f64(dp, 1, M, N, ldo, st));
+      return LNO_OT_OK;
+    }
+    TcProb p{};
+    p.nseg = 1;
+    p.seg[0] = TcSeg{0, 0, (int)l0, (int)r0, naux, 0};
+    p.out = amax_pass ? nullptr : out;
+    TcProb* dp;
+    TRY(arena.get(&dp, 1));
+    CU(cudaMemcpyAsync(dp, &p, sizeof p, cudaMemcpyHostToDevice, st));
+    CUtensorMap mA[2] = {Lo.mapA, Lo.mapA}, mB[2] = {Ro.mapB128, Ro.mapB128};
+    const double scale = sigB * sigB * std::ldexp(1.0, -14);
+    CU(launch_tc_gemm<4, 128, double>(mA, mB, dp, 1, M, N, ldo, scale, ctx->d_flag,
+                                      amax_pass ? ctx->d_amax : nullptr, ctx->nsm, st));
+    return LNO_OT_OK;
+  }
+
+  // ---- stage ----------------------------------------------------------------
+  int stage() {
+    nbas = dom->nbas;
+    naux = dom->naux;
+    for (int s = 0; s < 2; ++s) {
+      no[s] = dom->nocc[s];
+      nv[s] = nbas - no[s];
+    }
+    if (!f64) {  // global scales of B and T2
+      CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), st));
+      for (int s = 0; s < 2; ++s)
+        CU(launch_absmax(dom->B[s], (int64_t)naux * nbas * nbas, ctx->d_amax, st));
+      unsigned long long h;
+      CU(cudaMemcpyAsync(&h, ctx->d_amax, sizeof h, cudaMemcpyDeviceToHost, st));
+      CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), st));
+      CU(launch_absmax(dom->t2aa, (int64_t)no[0] * no[0] * nv[0] * nv[0], ctx->d_amax, st));
+      CU(launch_absmax(dom->t2bb, (int64_t)no[1] * no[1] * nv[1] * nv[1], ctx->d_amax, st));
+      CU(launch_absmax(dom->t2ab, (int64_t)no[0] * no[1] * nv[0] * nv[1], ctx->d_amax, st));
+      unsigned long long ht;
+      CU(cudaMemcpyAsync(&ht, ctx->d_amax, sizeof ht, cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      double mb, mt;
+      std::memcpy(&mb, &h, 8);
+      std::memcpy(&mt, &ht, 8);
+      sigB = pow2_scale(mb);
+      sigT = pow2_scale(mt);
+      stats->other_launches += 5;
+    }
+    for (int s = 0; s < 2; ++s) {
+      const int o = no[s], v = nv[s];
+      TRY(alloc_operand(Boo[s], 1, (int64_t)o * o, naux, Sdf));
+      TRY(alloc_operand(Bov[s], 1, (int64_t)o * v, naux, Sdf));
+      TRY(alloc_operand(Bvv[s], 1, (int64_t)v * v, naux, Sdf));
+      struct Blk {
+        Operand* op;
+        int p0, np, q0, nq;
+      } blks[3] = {{&Boo[s], 0, o, 0, o}, {&Bov[s], 0, o, o, v}, {&Bvv[s], o, v, o, v}};
+      for (auto& b : blks) {
+        stats->other_launches++;
+        if (f64)
+          CU(launch_transpose_block(dom->B[s], naux, nbas, b.p0, b.np, b.q0, b.nq, b.op->Kp,
+                                    StoreF64{b.op->f64}, st));
+        else
+          CU(launch_transpose_block(
+              dom->B[s], naux, nbas, b.p0, b.np, b.q0, b.nq, b.op->Kp,
+              StoreSlices<4>{b.op->bf, b.op->slice_stride, 128.0 / sigB, 128.0 / sigB}, st));
+      }
+    }
+    for (int s = 0; s < 2; ++s) {  // (ia|jb) of spin s
+      const int64_t n = (int64_t)no[s] * nv[s];
+      TRY(arena.get(&ovov_ss[s], (size_t)std::max<int64_t>(n * n, 1)));
+      TRY(df(Bov[s], 0, (int)n, Bov[s], 0, (int)n, ovov_ss[s], (int)n));
+    }
+    return LNO_OT_OK;
+  }
+};
+
+// Spin-case triplet selection.
+struct CaseSel {
+  std::vector<Trip> trips;   // triplets to compute, in output order
+  int64_t ntot = 0;          // all restricted triplets of the case
+};
+
+int64_t c2(int64_t n) { return n * (n - 1) / 2; }
+int64_t c3(int64_t n) { return n * (n - 1) * (n - 2) / 6; }
+
+Trip decode_triplet(int c, int64_t q, int na, int nb) {
+  // lexicographic enumeration as in the header
+  auto same = [](int64_t q, int n) {
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) {
+        int64_t cnt = n - j - 1;
+        if (q < cnt) return Trip{i, j, (int)(j + 1 + q)};
+        q -= cnt;
+      }
+    return Trip{-1, -1, -1};
+  };
+  auto mixed = [](int64_t q, int n2, int n1) {
+    int64_t pairi = q / n1;
+    int k = (int)(q % n1);
+    for (int i = 0; i < n2; ++i) {
+      int64_t cnt = n2 - i - 1;
+      if (pairi < cnt) return Trip{i, (int)(i + 1 + pairi), k};
+      pairi -= cnt;
+    }
+    return Trip{-1, -1, -1};
+  };
+  switch (c) {
+    case 0: return same(q, na);
+    case 3: return same(q, nb);
+    case 1: return mixed(q, na, nb);
+    default: return mixed(q, nb, na);
+  }
+}
+
+int select_case(const lno_ot_domain* d, int c, CaseSel& cs) {
+  const int na = d->nocc[0], nb = d->nocc[1];
+  cs.ntot = c == 0 ? c3(na) : c == 3 ? c3(nb) : c == 1 ? c2(na) * nb : c2(nb) * na;
+  cs.trips.clear();
+  if (d->trip_sel[c]) {
+    if (d->n_sel[c] < 0) return LNO_OT_EINVAL;
+    cs.trips.reserve((size_t)d->n_sel[c]);
+    for (int64_t q = 0; q < d->n_sel[c]; ++q) {
+      int64_t id = d->trip_sel[c][q];
+      if (id < 0 || id >= cs.ntot) return LNO_OT_EINVAL;
+      cs.trips.push_back(decode_triplet(c, id, na, nb));
+    }
+  } else {
+    // enumerate directly (fast path)
+    if (c == 0 || c == 3) {
+      const int n = c == 0 ? na : nb;
+      for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+          for (int k = j + 1; k < n; ++k) cs.trips.push_back(Trip{i, j, k});
+    } else {
+      const int n2 = c == 1 ? na : nb, n1 = c == 1 ? nb : na;
+      for (int i = 0; i < n2; ++i)
+        for (int j = i + 1; j < n2; ++j)
+          for (int k = 0; k < n1; ++k) cs.trips.push_back(Trip{i, j, k});
+    }
+  }
+  return LNO_OT_OK;
+}
+
+double flops_alg_same(double v, double o) { return 3.0 * (2 * v * v * v * v + 2 * v * v * v * o); }
+double flops_alg_mixed(double vs, double vt, double os, double ot) {
+  return 4 * vs * vs * vt * vt + 6 * vs * vs * vs * vt + 4 * vs * vs * vt * ot + 6 * os * vs * vs * vt;
+}
+double kpad16(double k) { return std::ceil(k / 16.0) * 16.0; }
+
+// ----------------------------------------------------------------------------
+// Per spin s: same-spin case (sss) and the mixed case with two s orbitals.
+struct SpinPass {
+  Run& R;
+  int s, t;
+  int o, v, ot, vt;
+  CaseSel& same;   // case s==0 ? aaa : bbb
+  CaseSel& mixed;  // case s==0 ? aab : abb
+  double* e_same;  // per-triplet outputs (device)
+  double* e_mixed;
+
+  Operand AT, BT, A1, BG, BF, AT2;
+  std::vector<int> slotAT, slotBT, slotA1, slotBG, slotBF, slotAT2;  // -1 = unused
+  std::vector<int2> listAT, listA1, listAT2;
+  std::vector<int> listBT, listBG, listBF;
+  double* t2st = nullptr;    // [os][ot][vs][vt]
+  const double* t2ss = nullptr;
+  double* ovov_ts = nullptr; // (jb|KC) as [ot][vt][os][vs]
+
+  Arena own;  // operands and temporaries of this spin pass
+
+  SpinPass(Run& r, int s_, CaseSel& sm, CaseSel& mx, double* es, double* em)
+      : R(r), s(s_), t(1 - s_), same(sm), mixed(mx), e_same(es), e_mixed(em),
+        own(r.st, 0) {
+    o = R.no[s];
+    v = R.nv[s];
+    ot = R.no[t];
+    vt = R.nv[t];
+  }
+
+  void plan() {
+    listAT.clear();
+    listA1.clear();
+    listAT2.clear();
+    listBT.clear();
+    listBG.clear();
+    listBF.clear();
+    slotAT.assign((size_t)o * o, -1);
+    slotBT.assign(o, -1);
+    slotA1.assign((size_t)o * ot, -1);
+    slotBG.assign(o, -1);
+    slotBF.assign(ot, -1);
+    slotAT2.assign((size_t)o * ot, -1);
+    auto need_pair = [&](std::vector<int>& slot, std::vector<int2>& list, int p, int q, int w) {
+      int& sl = slot[(size_t)p * w + q];
+      if (sl < 0) {
+        sl = (int)list.size();
+        list.push_back(make_int2(p, q));
+      }
+    };
+    auto need_one = [&](std::vector<int>& slot, std::vector<int>& list, int x) {
+      if (slot[x] < 0) {
+        slot[x] = (int)list.size();
+        list.push_back(x);
+      }
+    };
+    for (const Trip& tr : same.trips) {
+      need_pair(slotAT, listAT, tr.j, tr.k, o);
+      need_pair(slotAT, listAT, tr.k, tr.i, o);
+      need_pair(slotAT, listAT, tr.i, tr.j, o);
+      need_one(slotBT, listBT, tr.i);
+      need_one(slotBT, listBT, tr.j);
+      need_one(slotBT, listBT, tr.k);
+    }
+    for (const Trip& tr : mixed.trips) {
+      need_pair(slotA1, listA1, tr.j, tr.k, ot);
+      need_pair(slotA1, listA1, tr.i, tr.k, ot);
+      need_one(slotBG, listBG, tr.i);
+      need_one(slotBG, listBG, tr.j);
+      need_pair(slotAT, listAT, tr.i, tr.j, o);
+      need_one(slotBF, listBF, tr.k);
+      need_pair(slotAT2, listAT2, tr.j, tr.k, ot);
+      need_pair(slotAT2, listAT2, tr.i, tr.k, ot);
+      need_one(slotBT, listBT, tr.i);
+      need_one(slotBT, listBT, tr.j);
+    }
+  }
+
+  template <class St>
+  int pack_all(St stAT, St stBT, St stA1, St stBG, St stBF, St stAT2) {
+    Arena& A = own;
+    cudaStream_t st = R.st;
+    // ---- same-spin operands -------------------------------------------------
+    if (!listAT.empty()) {
+      double* oovoT;
+      TRY(A.get(&oovoT, (size_t)o * v * o * o));
+      TRY(R.df(R.Boo[s], 0, o * o, R.Bov[s], 0, o * v, oovoT, o * o));
+      if (!R.amax_pass) {
+        int2* dl;
+        TRY(A.get(&dl, listAT.size()));
+        CU(cudaMemcpyAsync(dl, listAT.data(), listAT.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, st));
+        R.stats->other_launches++;
+        CU(launch_pack_at_same(dl, (int)listAT.size(), o, v, AT.Kp, t2ss, oovoT, stAT, st));
+      }
+      A.drop(oovoT);
+    }
+    if (!listBT.empty()) {
+      double* vvovT;
+      TRY(A.get(&vvovT, (size_t)v * v * v));
+      for (size_t q = 0; q < listBT.size(); ++q) {
+        const int x = listBT[q];
+        TRY(R.df(R.Bvv[s], 0, v * v, R.Bov[s], (int64_t)x * v, v, vvovT, v * v));
+        if (!R.amax_pass) {
+          R.stats->other_launches++;
+          CU(launch_pack_bt_same((int)q, x, o, v, BT.Kp, vvovT, t2ss, stBT, st));
+        }
+      }
+      A.drop(vvovT);
+    }
+    // ---- mixed operands -----------------------------------------------------
+    if (!listA1.empty()) {
+      double* jT;
+      TRY(A.get(&jT, (size_t)o * v * ot * ot));
+      TRY(R.df(R.Bov[s], 0, o * v, R.Boo[t], 0, ot * ot, jT, o * v));
+      if (!R.amax_pass) {
+        int2* dl;
+        TRY(A.get(&dl, listA1.size()));
+        CU(cudaMemcpyAsync(dl, listA1.data(), listA1.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, st));
+        R.stats->other_launches++;
+        CU(launch_pack_a1(dl, (int)listA1.size(), o, v, ot, vt, A1.Kp, t2st, jT, stA1, st));
+      }
+      A.drop(jT);
+    }
+    if (!listBG.empty()) {
+      double* gT;
+      TRY(A.get(&gT, (size_t)v * vt * vt));
+      for (size_t q = 0; q < listBG.size(); ++q) {
+        const int x = listBG[q];
+        TRY(R.df(R.Bvv[t], 0, vt * vt, R.Bov[s], (int64_t)x * v, v, gT, vt * vt));
+        if (!R.amax_pass) {
+          R.stats->other_launches++;
+          CU(launch_pack_bg((int)q, x, o, v, ot, vt, BG.Kp, gT, t2st, stBG, st));
+        }
+      }
+      A.drop(gT);
+    }
+    if (!listBF.empty()) {
+      double* fT;
+      TRY(A.get(&fT, (size_t)vt * v * v));
+      for (size_t q = 0; q < listBF.size(); ++q) {
+        const int K = listBF[q];
+        TRY(R.df(R.Bvv[s], 0, v * v, R.Bov[t], (int64_t)K * vt, vt, fT, v * v));
+        if (!R.amax_pass) {
+          R.stats->other_launches++;
+          CU(launch_pack_bf((int)q, K, o, v, ot, vt, BF.Kp, fT, t2st, stBF, st));
+        }
+      }
+      A.drop(fT);
+    }
+    if (!listAT2.empty()) {
+      double* lT;
+      TRY(A.get(&lT, (size_t)ot * vt * o * o));
+      TRY(R.df(R.Boo[s], 0, o * o, R.Bov[t], 0, ot * vt, lT, o * o));
+      if (!R.amax_pass) {
+        int2* dl;
+        TRY(A.get(&dl, listAT2.size()));
+        CU(cudaMemcpyAsync(dl, listAT2.data(), listAT2.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, st));
+        R.stats->other_launches++;
+        CU(launch_pack_at2(dl, (int)listAT2.size(), o, v, ot, vt, AT2.Kp, t2st, lT, stAT2, st));
+      }
+      A.drop(lT);
+    }
+    return LNO_OT_OK;
+  }
+
+  int prepare_inputs() {
+    t2ss = s == 0 ? R.dom->t2aa : R.dom->t2bb;
+    if (!mixed.trips.empty() && t2st == nullptr) {
+      if (s == 0) {
+        t2st = const_cast<double*>(R.dom->t2ab);
+      } else {
+        TRY(own.get(&t2st, (size_t)std::max<int64_t>((int64_t)o * ot * v * vt, 1)));
+        R.stats->other_launches++;
+        CU(launch_transpose_t2ab(R.dom->t2ab, ot, o, vt, v, t2st, R.st));
+      }
+    }
+    return LNO_OT_OK;
+  }
+
+  // measure integral magnitudes (sliced path, first pass)
+  int measure() {
+    if (listAT.empty() && listBT.empty() && listA1.empty() && listBG.empty() && listBF.empty() &&
+        listAT2.empty())
+      return LNO_OT_OK;
+    R.amax_pass = true;
+    StoreF64 dummy{nullptr};
+    int rc = pack_all(dummy, dummy, dummy, dummy, dummy, dummy);
+    R.amax_pass = false;
+    return rc;
+  }
+
+  int build() {
+    TRY(R.alloc_operand(own, AT, (int)listAT.size(), v, v + o, R.S));
+    TRY(R.alloc_operand(own, BT, (int)listBT.size(), npairs(v), v + o, R.S));
+    TRY(R.alloc_operand(own, A1, (int)listA1.size(), v, vt + ot, R.S));
+    TRY(R.alloc_operand(own, BG, (int)listBG.size(), (int64_t)v * vt, vt + ot, R.S));
+    TRY(R.alloc_operand(own, BF, (int)listBF.size(), (int64_t)v * vt, v + o, R.S));
+    TRY(R.alloc_operand(own, AT2, (int)listAT2.size(), vt, v + o, R.S));
+    if (R.f64) return pack_all(StoreF64{AT.f64}, StoreF64{BT.f64}, StoreF64{A1.f64},
+                               StoreF64{BG.f64}, StoreF64{BF.f64}, StoreF64{AT2.f64});
+    if (R.S == 2)
+      return pack_all(R.slices<2>(AT), R.slices<2>(BT), R.slices<2>(A1), R.slices<2>(BG),
+                      R.slices<2>(BF), R.slices<2>(AT2));
+    return pack_all(R.slices<3>(AT), R.slices<3>(BT), R.slices<3>(A1), R.slices<3>(BG),
+                    R.slices<3>(BF), R.slices<3>(AT2));
+  }
+
+  // ---- contraction launches -------------------------------------------------
+  int contract(int nprob, int M, int N, int ldo, const Operand& opA0, const Operand& opA1,
+               const Operand& opB0, const Operand& opB1, const std::vector<ProbF64>& pf,
+               const std::vector<TcProb>& pt, ProbF64* dpf, TcProb* dpt) {
+    cudaEvent_t e0 = R.event(), e1 = R.event();
+    if (e0) cudaEventRecord(e0, R.st);
+    if (R.f64) {
+      CU(cudaMemcpyAsync(dpf, pf.data(), nprob * sizeof(ProbF64), cudaMemcpyHostToDevice, R.st));
+      CU(launch_gemm_f64(dpf, nprob, M, N, ldo, R.st));
+    } else {
+      CU(cudaMemcpyAsync(dpt, pt.data(), nprob * sizeof(TcProb), cudaMemcpyHostToDevice, R.st));
+      CUtensorMap mA[2] = {opA0.mapA, opA1.mapA};
+      CUtensorMap mB[2] = {R.S == 2 ? opB0.mapB : opB0.mapB128, R.S == 2 ? opB1.mapB : opB1.mapB128};
+      const double scale = R.sigT * R.sigI * std::ldexp(1.0, -14);
+      if (R.S == 2)
+        CU(launch_tc_gemm<2, 256, float>(mA, mB, dpt, nprob, M, N, ldo, scale, R.ctx->d_flag,
+                                         nullptr, R.ctx->nsm, R.st));
+      else
+        CU(launch_tc_gemm<3, 128, float>(mA, mB, dpt, nprob, M, N, ldo, scale, R.ctx->d_flag,
+                                         nullptr, R.ctx->nsm, R.st));
+    }
+    if (e1) cudaEventRecord(e1, R.st);
+    if (e0 && e1) R.contract_ev.push_back({e0, e1});
+    R.stats->contract_launches++;
+    return LNO_OT_OK;
+  }
+
+  void seg_f64(SegF64& sg, const Operand& A, int64_t arow, const Operand& B, int64_t brow,
+               double sign) {
+    sg = SegF64{A.f64 + arow * A.Kp, B.f64 + brow * B.Kp, A.K, A.Kp, B.Kp, sign};
+  }
+  void seg_tc(TcSeg& sg, int amap, const Operand& A, int64_t arow, int bmap, const Operand& B,
+              int64_t brow, int neg) {
+    sg = TcSeg{amap, bmap, (int)arow, (int)brow, A.K, neg};
+  }
+
+  int run_case(bool is_mixed) {
+    CaseSel& cs = is_mixed ? mixed : same;
+    const int ntrip = (int)cs.trips.size();
+    if (ntrip == 0) return LNO_OT_OK;
+    Arena A(R.st, 0);  // per-case buffers
+    const bool f64 = R.f64;
+    const size_t esz = f64 ? 8 : 4;
+    // output layouts
+    const int M1 = v;                                       // rows a
+    const int64_t N1 = is_mixed ? (int64_t)v * vt : npairs(v);
+    const int P1 = (int)round_up(std::max(M1, 1), 16);
+    const int M2 = vt;                                      // mixed Z': rows C
+    const int64_t N2 = is_mixed ? npairs(v) : 0;
+    const int P2 = (int)round_up(std::max(M2, 1), 16);
+    const int64_t per_trip = (N1 * P1 + N2 * P2) * (int64_t)esz;
+    const int64_t budget = (int64_t)6 << 30;
+    int G = (int)std::max<int64_t>(1, std::min<int64_t>(64, budget / std::max<int64_t>(per_trip, 1)));
+    G = std::min(G, ntrip);
+    char *X = nullptr, *Z = nullptr;
+    TRY(A.get(&X, (size_t)(G * N1 * P1 * esz) + 64));
+    if (is_mixed) TRY(A.get(&Z, (size_t)(G * N2 * P2 * esz) + 64));
+    CU(cudaMemsetAsync(X, 0, (size_t)(G * N1 * P1 * esz), R.st));
+    if (is_mixed) CU(cudaMemsetAsync(Z, 0, (size_t)(G * N2 * P2 * esz), R.st));
+    // cube tiles
+    std::vector<int3> blocks;
+    const int nbs = (v + 15) / 16, nbt = (vt + 15) / 16;
+    if (!is_mixed) {
+      for (int a = 0; a < nbs; ++a)
+        for (int b = a; b < nbs; ++b)
+          for (int c = b; c < nbs; ++c) blocks.push_back(make_int3(a, b, c));
+    } else {
+      for (int a = 0; a < nbs; ++a)
+        for (int b = a; b < nbs; ++b)
+          for (int c = 0; c < nbt; ++c) blocks.push_back(make_int3(a, b, c));
+    }
+    if (blocks.empty()) {  // no virtual orbitals in this case: every W is empty
+      CU(cudaMemsetAsync(is_mixed ? e_mixed : e_same, 0, (size_t)ntrip * sizeof(double), R.st));
+      return LNO_OT_OK;
+    }
+    int3* dblocks;
+    TRY(A.get(&dblocks, blocks.size()));
+    CU(cudaMemcpyAsync(dblocks, blocks.data(), blocks.size() * sizeof(int3),
+                       cudaMemcpyHostToDevice, R.st));
+    Trip* dtrips;
+    TRY(A.get(&dtrips, (size_t)ntrip));
+    CU(cudaMemcpyAsync(dtrips, cs.trips.data(), ntrip * sizeof(Trip), cudaMemcpyHostToDevice,
+                       R.st));
+    const int target = R.ctx->nsm * 6;
+    const int P = std::max(1, std::min((int)blocks.size(), target / G + 1));
+    double* partial;
+    TRY(A.get(&partial, (size_t)G * P));
+    // float32 V tables of the tensor-core path, per triplet
+    const int pv = (int)round_up(std::max(v, 1), 16), pvt = (int)round_up(std::max(vt, 1), 16);
+    const int64_t vt_stride = is_mixed ? round_up(2LL * v * pvt + (int64_t)v * pv, 16)
+                                       : 3LL * v * pv;
+    float* vtab = nullptr;
+    if (!f64) TRY(A.get(&vtab, (size_t)(G * vt_stride)));
+    ProbF64* dpf = nullptr;
+    TcProb* dpt = nullptr;
+    if (f64) {
+      TRY(A.get(&dpf, (size_t)G));
+    } else {
+      TRY(A.get(&dpt, (size_t)G));
+    }
+    std::vector<ProbF64> pf(G), pf2(G);
+    std::vector<TcProb> pt(G), pt2(G);
+    double* eout = is_mixed ? e_mixed : e_same;
+
+    EnergyArgs ea{};
+    ea.kind = is_mixed ? MIXED : SAME;
+    ea.nvs = v;
+    ea.nvt = is_mixed ? vt : v;
+    ea.nos = o;
+    ea.not_ = is_mixed ? ot : o;
+    ea.eps_s = R.dom->eps[s];
+    ea.eps_t = R.dom->eps[is_mixed ? t : s];
+    ea.t1s = R.dom->t1[s];
+    ea.t1t = R.dom->t1[is_mixed ? t : s];
+    ea.ovov_ss = R.ovov_ss[s];
+    ea.ovov_ts = ovov_ts;
+    ea.blocks = dblocks;
+    ea.nblocks = (int)blocks.size();
+    ea.pitch_x = P1;
+    ea.pitch_z = P2;
+    ea.x_stride = N1 * P1;
+    ea.z_stride = N2 * P2;
+
+    // stats
+    const double dv = v, dvt = vt, dov = o, dot = ot;
+    const double alg = is_mixed ? flops_alg_mixed(dv, dvt, dov, dot) : flops_alg_same(dv, dov);
+    const double exe = is_mixed ? 2.0 * dv * (dv * dvt) * (2 * (dvt + dot) + dv + dov) +
+                                      2.0 * dvt * (double)npairs(v) * 2 * (dv + dov)
+                                : 2.0 * dv * (double)npairs(v) * 3 * (dv + dov);
+    const double tens = is_mixed ? 2.0 * dv * (dv * dvt) * (2 * kpad16(dvt + dot) + kpad16(dv + dov)) +
+                                       2.0 * dvt * (double)npairs(v) * 2 * kpad16(dv + dov)
+                                 : 2.0 * dv * (double)npairs(v) * 3 * kpad16(dv + dov);
+    R.stats->flops_algorithmic += alg * ntrip;
+    R.stats->flops_executed += exe * ntrip;
+    if (!f64) R.stats->tensor_flops += tens * ntrip * (R.S * (R.S + 1) / 2);
+    R.stats->triplets += ntrip;
+    R.stats->elements += (int64_t)ntrip *
+                         (is_mixed ? npairs(v) * vt : (int64_t)v * (v - 1) * (v - 2) / 6);
+
+    for (int g0 = 0; g0 < ntrip; g0 += G) {
+      const int ng = std::min(G, ntrip - g0);
+      for (int g = 0; g < ng; ++g) {
+        const Trip tr = cs.trips[g0 + g];
+        const int i = tr.i, j = tr.j, k = tr.k;
+        char* Xg = X + (size_t)g * N1 * P1 * esz;
+        if (!is_mixed) {
+          const int64_t r_jk = (int64_t)slotAT[(size_t)j * o + k] * v;
+          const int64_t r_ki = (int64_t)slotAT[(size_t)k * o + i] * v;
+          const int64_t r_ij = (int64_t)slotAT[(size_t)i * o + j] * v;
+          const int64_t b_i = slotBT[i] * npairs(v), b_j = slotBT[j] * npairs(v),
+                        b_k = slotBT[k] * npairs(v);
+          if (f64) {
+            ProbF64& p = pf[g];
+            p.nseg = 3;
+            seg_f64(p.seg[0], AT, r_jk, BT, b_i, 1.0);
+            seg_f64(p.seg[1], AT, r_ki, BT, b_j, 1.0);
+            seg_f64(p.seg[2], AT, r_ij, BT, b_k, 1.0);
+            p.XT = reinterpret_cast<double*>(Xg);
+          } else {
+            TcProb& p = pt[g];
+            p.nseg = 3;
+            seg_tc(p.seg[0], 0, AT, r_jk, 0, BT, b_i, 0);
+            seg_tc(p.seg[1], 0, AT, r_ki, 0, BT, b_j, 0);
+            seg_tc(p.seg[2], 0, AT, r_ij, 0, BT, b_k, 0);
+            p.out = Xg;
+          }
+        } else {
+          const int K = k;
+          const int64_t a1_jK = (int64_t)slotA1[(size_t)j * ot + K] * v;
+          const int64_t a1_iK = (int64_t)slotA1[(size_t)i * ot + K] * v;
+          const int64_t at_ij = (int64_t)slotAT[(size_t)i * o + j] * v;
+          const int64_t bg_i = (int64_t)slotBG[i] * v * vt, bg_j = (int64_t)slotBG[j] * v * vt;
+          const int64_t bf_K = (int64_t)slotBF[K] * v * vt;
+          const int64_t a2_jK = (int64_t)slotAT2[(size_t)j * ot + K] * vt;
+          const int64_t a2_iK = (int64_t)slotAT2[(size_t)i * ot + K] * vt;
+          const int64_t bt_i = slotBT[i] * npairs(v), bt_j = slotBT[j] * npairs(v);
+          char* Zg = Z + (size_t)g * N2 * P2 * esz;
+          if (f64) {
+            ProbF64& p = pf[g];
+            p.nseg = 3;
+            seg_f64(p.seg[0], A1, a1_jK, BG, bg_i, 1.0);
+            seg_f64(p.seg[1], A1, a1_iK, BG, bg_j, -1.0);
+            seg_f64(p.seg[2], AT, at_ij, BF, bf_K, 1.0);
+            p.XT = reinterpret_cast<double*>(Xg);
+            ProbF64& q = pf2[g];
+            q.nseg = 2;
+            seg_f64(q.seg[0], AT2, a2_jK, BT, bt_i, -1.0);
+            seg_f64(q.seg[1], AT2, a2_iK, BT, bt_j, 1.0);
+            q.XT = reinterpret_cast<double*>(Zg);
+          } else {
+            TcProb& p = pt[g];
+            p.nseg = 3;
+            seg_tc(p.seg[0], 0, A1, a1_jK, 0, BG, bg_i, 0);
+            seg_tc(p.seg[1], 0, A1, a1_iK, 0, BG, bg_j, 1);
+            seg_tc(p.seg[2], 1, AT, at_ij, 1, BF, bf_K, 0);
+            p.out = Xg;
+            TcProb& q = pt2[g];
+            q.nseg = 2;
+            seg_tc(q.seg[0], 0, AT2, a2_jK, 0, BT, bt_i, 1);
+            seg_tc(q.seg[1], 0, AT2, a2_iK, 0, BT, bt_j, 0);
+            q.out = Zg;
+          }
+        }
+      }
+      if (!is_mixed) {
+        TRY(contract(ng, M1, (int)N1, P1, AT, AT, BT, BT, pf, pt, dpf, dpt));
+      } else {
+        TRY(contract(ng, M1, (int)N1, P1, A1, AT, BG, BF, pf, pt, dpf, dpt));
+        ProbF64* dpf2 = nullptr;
+        TcProb* dpt2 = nullptr;
+        // second problem list uses its own device array (the first may still be read)
+        if (f64) {
+          TRY(A.get(&dpf2, (size_t)ng));
+        } else {
+          TRY(A.get(&dpt2, (size_t)ng));
+        }
+        TRY(contract(ng, M2, (int)N2, P2, AT2, AT2, BT, BT, pf2, pt2, dpf2, dpt2));
+        A.drop(f64 ? (void*)dpf2 : (void*)dpt2);
+      }
+      // energy
+      ea.trips = dtrips + g0;
+      ea.partial = partial;
+      cudaEvent_t e0 = R.event(), e1 = R.event();
+      if (e0) cudaEventRecord(e0, R.st);
+      if (f64)
+        CU(launch_energy(ea, X, Z, f64, ng, P, R.st));
+      else
+        CU(launch_energy_f32(ea, reinterpret_cast<const float*>(X),
+                             reinterpret_cast<const float*>(Z), vtab, vt_stride, pv, pvt, ng, P,
+                             R.st));
+      CU(launch_reduce_partials(partial, P, ng, eout + g0, R.st));
+      if (e1) cudaEventRecord(e1, R.st);
+      if (e0 && e1) R.energy_ev.push_back({e0, e1});
+      R.stats->energy_launches += 2;
+      // the host reuses pf/pt for the next group: make sure the copy is done
+      CU(cudaStreamSynchronize(R.st));
+    }
+    return LNO_OT_OK;
+  }
+
+  int run() {
+    if (same.trips.empty() && mixed.trips.empty()) return LNO_OT_OK;
+    plan();
+    TRY(prepare_inputs());
+    if (!mixed.trips.empty()) {
+      const int64_t nr = (int64_t)o * v, nc = (int64_t)ot * vt;
+      TRY(own.get(&ovov_ts, (size_t)std::max<int64_t>(nr * nc, 1)));
+      TRY(R.df(R.Bov[s], 0, (int)nr, R.Bov[t], 0, (int)nc, ovov_ts, (int)nr));
+    }
+    TRY(build());
+    TRY(run_case(false));
+    TRY(run_case(true));
+    return LNO_OT_OK;
+  }
+};
+
+int check_ptr(const lno_ot_ctx* ctx, const void* p, bool required) {
+  if (!p) return required ? LNO_OT_EINVAL : LNO_OT_OK;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return LNO_OT_EDEVICE;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return LNO_OT_EDEVICE;
+  if (at.device != ctx->device) return LNO_OT_EDEVICE;
+  return LNO_OT_OK;
+}
+
+int validate(const lno_ot_ctx* ctx, const lno_ot_domain* d) {
+  if (!d) return LNO_OT_EINVAL;
+  if (d->nbas <= 0 || d->naux <= 0) return LNO_OT_EINVAL;
+  if (d->nocc[1] < 0 || d->nocc[1] > d->nocc[0] || d->nocc[0] > d->nbas) return LNO_OT_EINVAL;
+  if ((int64_t)d->nbas * d->nbas * d->naux > ((int64_t)1 << 40)) return LNO_OT_EINVAL;
+  if (d->fov[0] || d->fov[1]) return LNO_OT_EUNSUPPORTED;
+  for (int s = 0; s < 2; ++s) {
+    TRY(check_ptr(ctx, d->B[s], true));
+    TRY(check_ptr(ctx, d->eps[s], true));
+    const bool need_t1 = d->nocc[s] > 0 && d->nocc[s] < d->nbas;
+    TRY(check_ptr(ctx, d->t1[s], need_t1));
+  }
+  const bool va = d->nocc[0] < d->nbas, vb = d->nocc[1] < d->nbas;
+  TRY(check_ptr(ctx, d->t2aa, d->nocc[0] > 0 && va));
+  TRY(check_ptr(ctx, d->t2bb, d->nocc[1] > 0 && vb));
+  TRY(check_ptr(ctx, d->t2ab, d->nocc[0] > 0 && d->nocc[1] > 0 && va && vb));
+  for (int c = 0; c < 4; ++c) TRY(check_ptr(ctx, d->e_trip[c], false));
+  return LNO_OT_OK;
+}
+
+int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
+  TRY(validate(ctx, dom));
+  if (ctx->prec == LNO_OT_TF32) return LNO_OT_EUNSUPPORTED;
+  CU(cudaSetDevice(ctx->device));
+  ctx->stats = lno_ot_stats{};
+  ctx->ev_used = 0;
+  Run R(ctx, dom);
+  R.f64 = ctx->prec == LNO_OT_FP64;
+  R.S = ctx->prec == LNO_OT_BF16X6 ? 3 : 2;
+  CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+  cudaEvent_t t0 = R.event(), t1 = R.event(), t2 = R.event();
+  if (t0) cudaEventRecord(t0, R.st);
+
+  CaseSel cs[4];
+  for (int c = 0; c < 4; ++c) TRY(select_case(dom, c, cs[c]));
+  double* e_int[4];
+  for (int c = 0; c < 4; ++c)
+    TRY(R.arena.get(&e_int[c], std::max<size_t>(cs[c].trips.size(), 1)));
+  TRY(R.stage());
+  {
+    SpinPass pa(R, 0, cs[0], cs[1], e_int[0], e_int[1]);
+    SpinPass pb(R, 1, cs[3], cs[2], e_int[3], e_int[2]);
+    if (!R.f64) {  // integral scale: first pass over every DF block both spins need
+      pa.plan();
+      pb.plan();
+      TRY(pa.prepare_inputs());
+      TRY(pb.prepare_inputs());
+      CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), R.st));
+      TRY(pa.measure());
+      TRY(pb.measure());
+      unsigned long long h;
+      CU(cudaMemcpyAsync(&h, ctx->d_amax, sizeof h, cudaMemcpyDeviceToHost, R.st));
+      CU(cudaStreamSynchronize(R.st));
+      double m;
+      std::memcpy(&m, &h, 8);
+      R.sigI = pow2_scale(2.0 * m);  // antisymmetrised combinations are <= 2 max
+    }
+    if (t1) cudaEventRecord(t1, R.st);
+    TRY(pa.run());
+    pa.own.release();
+    TRY(pb.run());
+  }
+  // per-case sums
+  for (int c = 0; c < 4; ++c) {
+    if (cs[c].trips.empty()) {
+      CU(cudaMemsetAsync(ctx->d_sums + c, 0, sizeof(double), R.st));
+    } else {
+      CU(launch_neumaier_sum(e_int[c], (int64_t)cs[c].trips.size(), ctx->d_sums + c, R.st));
+      R.stats->other_launches++;
+      if (dom->e_trip[c])
+        CU(cudaMemcpyAsync(dom->e_trip[c], e_int[c], cs[c].trips.size() * sizeof(double),
+                           cudaMemcpyDeviceToDevice, R.st));
+    }
+  }
+  double hs[4];
+  CU(cudaMemcpyAsync(hs, ctx->d_sums, sizeof hs, cudaMemcpyDeviceToHost, R.st));
+  if (t2) cudaEventRecord(t2, R.st);
+  CU(cudaStreamSynchronize(R.st));
+  int flag = 0;
+  CU(cudaMemcpy(&flag, ctx->d_flag, sizeof flag, cudaMemcpyDeviceToHost));
+  if (flag) return LNO_OT_ETIMEOUT;
+  // stats
+  float ms = 0;
+  if (t0 && t2 && cudaEventElapsedTime(&ms, t0, t2) == cudaSuccess) ctx->stats.ms_total = ms;
+  if (t0 && t1 && cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess) ctx->stats.ms_stage = ms;
+  double acc = 0;
+  for (auto& p : R.contract_ev)
+    if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) acc += ms;
+  ctx->stats.ms_contract = acc;
+  acc = 0;
+  for (auto& p : R.energy_ev)
+    if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) acc += ms;
+  ctx->stats.ms_energy = acc;
+  // order: aaa, aab, abb, bbb, total (Neumaier on the host for the last 4)
+  double S = 0, Cc = 0;
+  for (int c = 0; c < 4; ++c) {
+    out->e[c] = hs[c];
+    double x = hs[c], tt = S + x;
+    Cc += std::fabs(S) >= std::fabs(x) ? (S - tt) + x : (x - tt) + S;
+    S = tt;
+  }
+  out->e[4] = S + Cc;
+  return LNO_OT_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
+  if (!ctx || !opt) return LNO_OT_EINVAL;
+  if (opt->precision < 0 || opt->precision > 3) return LNO_OT_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return LNO_OT_ECUDA;
+  }
+  if (opt->device < 0 || opt->device >= ndev) return LNO_OT_EDEVICE;
+  CU(cudaSetDevice(opt->device));
+  cudaDeviceProp prop;
+  CU(cudaGetDeviceProperties(&prop, opt->device));
+  if (opt->precision != LNO_OT_FP64 && !(prop.major == 10 && prop.minor == 3))
+    return LNO_OT_EUNSUPPORTED;  // the tensor-core path is built for sm_103a only
+  lno_ot_ctx* c = new lno_ot_ctx();
+  c->device = opt->device;
+  c->prec = opt->precision;
+  c->ws_limit = opt->workspace_bytes;
+  c->nsm = prop.multiProcessorCount;
+  if (opt->stream) {
+    c->stream = static_cast<cudaStream_t>(opt->stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return LNO_OT_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  // keep freed stream-ordered memory in the pool between calls
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (cudaMalloc(&c->d_flag, 256) != cudaSuccess || cudaMalloc(&c->d_amax, 256) != cudaSuccess ||
+      cudaMalloc(&c->d_sums, 256) != cudaSuccess) {
+    cudaGetLastError();
+    lno_ot_destroy(c);
+    return LNO_OT_ENOMEM;
+  }
+  *ctx = c;
+  return LNO_OT_OK;
+}
+
+void lno_ot_destroy(lno_ot_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  cudaFree(c->d_flag);
+  cudaFree(c->d_amax);
+  cudaFree(c->d_sums);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int lno_ot_energy(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
+  if (!ctx || !out) return LNO_OT_EINVAL;
+  int rc = energy_impl(ctx, dom, out);
+  out->status = rc;
+  if (rc != LNO_OT_OK)
+    for (double& e : out->e) e = 0.0;
+  return rc;
+}
+
+int lno_ot_energy_batched(lno_ot_ctx* ctx, int ndom, const lno_ot_domain* doms,
+                          lno_ot_result* out) {
+  if (!ctx || ndom < 0 || (ndom > 0 && (!doms || !out))) return LNO_OT_EINVAL;
+  int first = LNO_OT_OK;
+  lno_ot_stats tot{};
+  for (int d = 0; d < ndom; ++d) {
+    int rc = lno_ot_energy(ctx, doms + d, out + d);
+    if (rc != LNO_OT_OK && first == LNO_OT_OK) first = rc;
+    const lno_ot_stats& s = ctx->stats;
+    tot.ms_total += s.ms_total;
+    tot.ms_stage += s.ms_stage;
+    tot.ms_contract += s.ms_contract;
+    tot.ms_energy += s.ms_energy;
+    tot.flops_algorithmic += s.flops_algorithmic;
+    tot.flops_executed += s.flops_executed;
+    tot.tensor_flops += s.tensor_flops;
+    tot.contract_launches += s.contract_launches;
+    tot.energy_launches += s.energy_launches;
+    tot.other_launches += s.other_launches;
+    tot.triplets += s.triplets;
+    tot.elements += s.elements;
+  }
+  ctx->stats = tot;
+  return first;
+}
+
+int lno_ot_backward(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_grad* g) {
+  (void)gE;
+  if (!ctx || !dom || !g) return LNO_OT_EINVAL;
+  return LNO_OT_EUNSUPPORTED;
+}
+
+int lno_ot_last_stats(const lno_ot_ctx* ctx, lno_ot_stats* st) {
+  if (!ctx || !st) return LNO_OT_EINVAL;
+  *st = ctx->stats;
+  return LNO_OT_OK;
+}
+
+const char* lno_ot_strerror(int code) {
+  switch (code) {
+    case LNO_OT_OK: return "ok";
+    case LNO_OT_EINVAL: return "invalid argument (sizes, null pointer, nocc[1] > nocc[0])";
+    case LNO_OT_EDEVICE: return "pointer is not device memory of the context's device";
+    case LNO_OT_ENOMEM: return "device workspace allocation failed";
+    case LNO_OT_ECUDA: return "CUDA call failed";
+    case LNO_OT_ETIMEOUT: return "bounded device wait gave up";
+    case LNO_OT_EUNSUPPORTED: return "unsupported option or input";
+    default: return "unknown status";
+  }
+}
+
+const char* lno_ot_version(void) { return "lno_ot 0.1 sm_103a"; }
+
+int lno_ot_selftest_gemm(int device, int S, int M, int N, int K, const double* A, const double* B,
+                         double* Cout, void* stream) {
+  if (S < 1 || S > 4 || M <= 0 || N <= 0 || K <= 0 || !A || !B || !Cout) return LNO_OT_EINVAL;
+  CU(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  CU(cudaGetDeviceProperties(&prop, device));
+  if (!(prop.major == 10 && prop.minor == 3)) return LNO_OT_EUNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arena ar(st, 0);
+  unsigned long long* amax;
+  int* flag;
+  TRY(ar.get(&amax, 2));
+  TRY(ar.get(&flag, 1));
+  CU(cudaMemsetAsync(amax, 0, 16, st));
+  CU(cudaMemsetAsync(flag, 0, 4, st));
+  CU(launch_absmax(A, (int64_t)M * K, amax, st));
+  CU(launch_absmax(B, (int64_t)N * K, amax + 1, st));
+  unsigned long long h[2];
+  CU(cudaMemcpyAsync(h, amax, 16, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  double ma, mb;
+  std::memcpy(&ma, &h[0], 8);
+  std::memcpy(&mb, &h[1], 8);
+  const double sa = pow2_scale(ma), sb = pow2_scale(mb);
+  const int Kp = (int)round_up(K, 8);
+  const int64_t na = round_up((int64_t)M * Kp, 8), nb = round_up((int64_t)N * Kp, 8);
+  __nv_bfloat16 *a16, *b16;
+  TRY(ar.get(&a16, (size_t)(na * S)));
+  TRY(ar.get(&b16, (size_t)(nb * S)));
+  // slice on the host (diagnostic path only; the product path slices on the GPU)
+  std::vector<double> ha((size_t)M * K), hb((size_t)N * K);
+  CU(cudaMemcpyAsync(ha.data(), A, ha.size() * 8, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(hb.data(), B, hb.size() * 8, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  std::vector<uint16_t> sa16((size_t)na * S, 0), sb16((size_t)nb * S, 0);
+  auto host_slices = [&](const std::vector<double>& src, int rows, std::vector<uint16_t>& dst,
+                         int64_t stride, double sc) {
+    for (int r = 0; r < rows; ++r)
+      for (int k = 0; k < K; ++k) {
+        double x = src[(size_t)r * K + k] * (128.0 / sc), w = 1.0;
+        for (int q = 0; q < S; ++q) {
+          double v = std::nearbyint(x * w) / w;
+          x -= v;
+          float f = (float)v;  // exact: at most 8 significant bits
+          uint32_t u;
+          std::memcpy(&u, &f, 4);
+          dst[(size_t)q * stride + (size_t)r * Kp + k] = (uint16_t)(u >> 16);
+          w *= 256.0;
+        }
+      }
+  };
+  host_slices(ha, M, sa16, na, sa);
+  host_slices(hb, N, sb16, nb, sb);
+  CU(cudaMemcpyAsync(a16, sa16.data(), sa16.size() * 2, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(b16, sb16.data(), sb16.size() * 2, cudaMemcpyHostToDevice, st));
+  CUtensorMap mA[2], mB[2];
+  TRY(make_operand_map(&mA[0], a16, Kp, M, S, na, 128));
+  TRY(make_operand_map(&mB[0], b16, Kp, N, S, nb, S <= 2 ? 256 : 128));
+  mA[1] = mA[0];
+  mB[1] = mB[0];
+  TcProb p{};
+  p.nseg = 1;
+  p.seg[0] = TcSeg{0, 0, 0, 0, K, 0};
+  p.out = Cout;
+  TcProb* dp;
+  TRY(ar.get(&dp, 1));
+  CU(cudaMemcpyAsync(dp, &p, sizeof p, cudaMemcpyHostToDevice, st));
+  const double scale = sa * sb * std::ldexp(1.0, -14);
+  int nsm = prop.multiProcessorCount;
+  switch (S) {
+    case 1: CU(launch_tc_gemm<1, 256, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st)); break;
+    case 2: CU(launch_tc_gemm<2, 256, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st)); break;
+    case 3: CU(launch_tc_gemm<3, 128, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st)); break;
+    default: CU(launch_tc_gemm<4, 128, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st));
+  }
+  int hflag = 0;
+  CU(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return hflag ? LNO_OT_ETIMEOUT : LNO_OT_OK;
+}
+
+const char* lno_ot_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

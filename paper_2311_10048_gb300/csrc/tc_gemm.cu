@@ -1,0 +1,450 @@
+// Tensor-core contraction for sm_103a: tcgen05.mma (BF16 x BF16 -> FP32 in
+// TMEM) fed by TMA, on exactly sliced float64 operands.
+//
+// Each float64 operand value is stored as S BF16 slices with a power-of-two
+// scale sigma (StoreSlices in common.cuh):
+//     x = sigma 2^-7 (s_0 + s_1 + ... + s_{S-1}),
+// s_0 an integer in [-128,128], s_1 a multiple of 2^-8 in [-1/2,1/2], ...
+// For C[m][n] = sum_k A[m][k] B[n][k] the kernel issues, per 16-wide k step,
+// the slice products (p,q) with p + q <= S-1 and accumulates each weight
+// class g = p + q in its own TMEM accumulator.  Every term of class g is an
+// integer multiple of 2^(-8g) no larger than 2^(14-8g), so each class sum is
+// exact (no rounding at all) while it needs at most 24 significant bits:
+// always for k <= 1024, and for random-sign data far beyond.  (Measured on sm_103a: a single FP32
+// accumulator shared by classes of different weight drifts by ~2^-17 of its
+// value over a few hundred MMAs, because each MMA rounds the running sum at
+// its own magnitude.)  The epilogue adds the classes from the smallest up in
+// float32 (the lower classes are ~2^-8 of the next, so this is one rounding
+// of the final sum) and scales by the power of two sigma_A sigma_B 2^-14.
+// Float64 output keeps HI and the rest separately (exact).  No float64
+// arithmetic runs per element: this GPU's FP64 rate is ~1/64 of FP32.  No
+// systematic bias enters the sum of ~1e12 positive-definite energy terms.
+//
+// A problem is XT[n][m] = sum_seg (+/-) A_seg[m][:] . B_seg[n][:]: up to 3
+// K-segments from different operand tensors (the three occupied
+// permutations of P(i/jk), or the mixed-spin terms); the sign is applied with
+// the instruction descriptor's negate-A bit.  Operand tensors are 3-D TMA
+// maps (k, row, slice); k beyond the tensor and rows beyond the last row
+// arrive as zeros.
+//
+// Kernel structure (one CTA per SM, persistent over tiles of 128 x BN):
+//   warp 0      TMA producer (one thread), STAGES-deep smem ring
+//   warp 1      TMEM allocator and MMA issuer (one thread); S accumulators
+//               of 128 x BN FP32 (BN = 256 for S <= 2, 128 for S >= 3)
+//   warps 2..5  epilogue: tcgen05.ld -> scale -> coalesced stores along m
+// Every mbarrier wait is bounded; on a timeout the kernel records an error
+// code, drains its own TMA copies and MMAs, frees TMEM and returns.
+#include "common.cuh"
+
+namespace lno {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 32;                     // 64-byte rows, SWIZZLE_64B
+constexpr long long kWaitCycles = 4000000000LL;
+constexpr int kSmemBudget = 227 * 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`; false if another role raised the error
+// flag (abortable) or the time limit passed (then records `code`).
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* flag, int code,
+                                       bool abortable) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (abortable && *(volatile int*)flag != 0) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        atomicCAS(flag, 0, code);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+      " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, rows of 64 B in
+// groups of 8 (stride 512 B between groups).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
+  d |= (uint64_t)4 << 61;            // SWIZZLE_64B
+  return d;
+}
+
+// Instruction descriptor: kind::f16, A/B BF16 K-major, D FP32, M=128, N=BN.
+template <int BN>
+__device__ __forceinline__ uint32_t idesc_bf16(int neg) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)neg << 13) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int S, int BN>
+struct Cfg {
+  static constexpr int kABytes = BM * BK * 2;          // one slice of A
+  static constexpr int kBBytes = BN * BK * 2;          // one slice of B
+  static constexpr int kStage = S * (kABytes + kBBytes);
+  static constexpr int kStages = (kSmemBudget - 2048) / kStage;
+  static constexpr int kSmem = kStages * kStage + 1024 + 256;
+  static constexpr int kProducts = S * (S + 1) / 2;
+  static_assert(kStages >= 2, "pipeline needs two stages");
+  static_assert(S * BN <= 512, "one TMEM accumulator per weight class");
+};
+
+template <int S, int BN, typename OutT>
+__global__ void __launch_bounds__(192, 1)
+tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+               const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
+               const TcProb* __restrict__ probs, int nprob, int M, int N, int ldo, double scale,
+               int* __restrict__ flag, unsigned long long* __restrict__ amax) {
+  using C = Cfg<S, BN>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStage);
+  // bars[0..st): full, [st..2st): empty, [2st]: tmem_full, [2st+1]: tmem_empty, [2st+2]: drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 3);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nM = (M + BM - 1) / BM, nN = (N + BN - 1) / BN;
+  const long long ntiles = (long long)nprob * nM * nN;
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + C::kStages + s); };
+  const uint32_t tfull = smem_u32(bars + 2 * C::kStages);
+  const uint32_t tempty = smem_u32(bars + 2 * C::kStages + 1);
+  const uint32_t drain = smem_u32(bars + 2 * C::kStages + 2);
+  auto a_addr = [&](int st, int sl) { return smem_u32(smem + st * C::kStage + sl * C::kABytes); };
+  auto b_addr = [&](int st, int sl) {
+    return smem_u32(smem + st * C::kStage + S * C::kABytes + sl * C::kBBytes);
+  };
+
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 128);
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------ producer -------------------------------
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, last_phase = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int mt = (int)(t % nM);
+        const long long r = t / nM;
+        const int nt = (int)(r % nN);
+        const TcProb& P = probs[r / nN];
+        for (int sg = 0; sg < P.nseg && ok; ++sg) {
+          const TcSeg seg = P.seg[sg];
+          const CUtensorMap* ma = seg.amap ? &mapA1 : &mapA0;
+          const CUtensorMap* mb = seg.bmap ? &mapB1 : &mapB0;
+          for (int k0 = 0; k0 < seg.K; k0 += BK) {
+            if (!mbar_wait(empty_bar(stage), phase ^ 1u, flag, 1, true)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(full_bar(stage), (uint32_t)C::kStage);
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl)
+              tma_load_3d(a_addr(stage, sl), ma, full_bar(stage), k0, seg.a_row + mt * BM, sl);
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl)
+              tma_load_3d(b_addr(stage, sl), mb, full_bar(stage), k0, seg.b_row + nt * BN, sl);
+            issued_mask |= 1u << stage;
+            last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
+            if (++stage == C::kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      // every copy this thread issued must have landed before smem goes away
+      for (int s = 0; s < C::kStages; ++s)
+        if (issued_mask & (1u << s)) mbar_wait(full_bar(s), (last_phase >> s) & 1u, flag, 4, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // -------------------------------- MMA ----------------------------------
+      int stage = 0;
+      uint32_t phase = 0, tile_it = 0;
+      bool ok = true, any = false;
+      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tile_it) {
+        const TcProb& P = probs[(t / nM) / nN];
+        if (tile_it > 0 && !mbar_wait(tempty, (tile_it - 1) & 1u, flag, 2, true)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        uint32_t cls_on = 0;  // bit g: accumulator of class g already written
+        for (int sg = 0; sg < P.nseg && ok; ++sg) {
+          const TcSeg seg = P.seg[sg];
+          const uint32_t idesc = idesc_bf16<BN>(seg.neg);
+          for (int k0 = 0; k0 < seg.K; k0 += BK) {
+            if (!mbar_wait(full_bar(stage), phase, flag, 3, true)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+              if (k0 + ks * 16 < seg.K) {
+#pragma unroll
+                for (int pa = 0; pa < S; ++pa) {
+#pragma unroll
+                  for (int pb = 0; pb + pa < S; ++pb) {
+                    const uint64_t ad = sdesc_sw64(a_addr(stage, pa) + ks * 32);
+                    const uint64_t bd = sdesc_sw64(b_addr(stage, pb) + ks * 32);
+                    const int g = pa + pb;
+                    umma_bf16(tmem + g * BN, ad, bd, idesc, (cls_on >> g) & 1u);
+                    cls_on |= 1u << g;
+                    any = true;
+                  }
+                }
+              }
+            }
+            umma_commit(empty_bar(stage));
+            if (++stage == C::kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+        if (ok) umma_commit(tfull);
+      }
+      if (!ok && any) {  // drain this thread's MMAs before TMEM is released
+        umma_commit(drain);
+        mbar_wait(drain, 0, flag, 5, false);
+      }
+    }
+  } else {
+    // ------------------------------- epilogue ---------------------------------
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    uint32_t tile_it = 0;
+    float lmax = 0.f;
+    // scale = sigma_A sigma_B 2^-14 is a power of two: exact in float
+    const float fscale = (float)scale;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_it) {
+      const int mt = (int)(t % nM);
+      const long long r = t / nM;
+      const int nt = (int)(r % nN);
+      const TcProb& P = probs[r / nN];
+      if (!mbar_wait(tfull, tile_it & 1u, flag, 6, true)) break;
+      tc_fence_after();
+      const int m = mt * BM + row;
+      OutT* out = reinterpret_cast<OutT*>(P.out);
+      const bool mok = m < M && out != nullptr;
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN / 16; ++c) {
+        uint32_t acc[S][16];
+#pragma unroll
+        for (int g = 0; g < S; ++g) tmem_ld16(tbase + g * BN + c * 16, acc[g]);
+        tmem_ld_wait();
+        const int n0 = nt * BN + c * 16;
+        OutT* op = out + (int64_t)n0 * ldo + m;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          // lower classes first (each exact), then one rounding against HI
+          float lo = 0.f;
+#pragma unroll
+          for (int g = S - 1; g >= 1; --g) lo = __fadd_rn(lo, __uint_as_float(acc[g][j]));
+          const float hi = __uint_as_float(acc[0][j]);
+          if constexpr (sizeof(OutT) == 4) {
+            const float v = __fmul_rn(__fadd_rn(hi, lo), fscale);
+            if (mok && n0 + j < N) op[(int64_t)j * ldo] = v;
+            if (amax != nullptr && m < M && n0 + j < N) lmax = fmaxf(lmax, fabsf(v));
+          } else {
+            if (mok && n0 + j < N)
+              op[(int64_t)j * ldo] = (double)__fmul_rn(hi, fscale) + (double)__fmul_rn(lo, fscale);
+            if (amax != nullptr && m < M && n0 + j < N)
+              lmax = fmaxf(lmax, fabsf(__fmul_rn(__fadd_rn(hi, lo), fscale)));
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(tempty);
+    }
+    if (amax != nullptr)
+      atomicMax(amax, (unsigned long long)__double_as_longlong((double)lmax));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3-D map over a sliced operand tensor: (k < Kp, row < rows, slice < S).
+// Box: 32 k x box_rows rows x 1 slice, 64-byte swizzle, zero fill.
+int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
+                     int64_t slice_stride, int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return LNO_OT_ECUDA;
+  if (Kp % 8 || slice_stride % 8 || (reinterpret_cast<uintptr_t>(base) & 15)) return LNO_OT_EINVAL;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)S};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(slice_stride * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? LNO_OT_OK : LNO_OT_ECUDA;
+}
+
+template <int S, int BN, typename OutT>
+cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
+                           int nprob, int M, int N, int ldo, double scale, int* flag,
+                           unsigned long long* amax, int nsm, cudaStream_t st) {
+  using C = Cfg<S, BN>;
+  if (nprob <= 0 || M <= 0 || N <= 0) return cudaSuccess;
+  auto k = tc_gemm_sliced<S, BN, OutT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (long long)nprob * ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int grid = (int)(ntiles < nsm ? ntiles : nsm);
+  k<<<grid, 192, C::kSmem, st>>>(mA[0], mA[1], mB[0], mB[1], probs_dev, nprob, M, N, ldo, scale,
+                                 flag, amax);
+  return cudaGetLastError();
+}
+
+int tc_products(int S) { return S * (S + 1) / 2; }
+
+template cudaError_t launch_tc_gemm<2, 256, float>(const CUtensorMap*, const CUtensorMap*,
+                                                   const TcProb*, int, int, int, int, double, int*,
+                                                   unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_tc_gemm<3, 128, float>(const CUtensorMap*, const CUtensorMap*,
+                                                   const TcProb*, int, int, int, int, double, int*,
+                                                   unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_tc_gemm<4, 128, double>(const CUtensorMap*, const CUtensorMap*,
+                                                    const TcProb*, int, int, int, int, double,
+                                                    int*, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_tc_gemm<1, 256, double>(const CUtensorMap*, const CUtensorMap*,
+                                                    const TcProb*, int, int, int, int, double,
+                                                    int*, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_tc_gemm<2, 256, double>(const CUtensorMap*, const CUtensorMap*,
+                                                    const TcProb*, int, int, int, int, double,
+                                                    int*, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_tc_gemm<3, 128, double>(const CUtensorMap*, const CUtensorMap*,
+                                                    const TcProb*, int, int, int, int, double,
+                                                    int*, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_tc_gemm<1, 256, float>(const CUtensorMap*, const CUtensorMap*,
+                                                   const TcProb*, int, int, int, int, double, int*,
+                                                   unsigned long long*, int, cudaStream_t);
+
+}  // namespace lno

@@ -1,0 +1,71 @@
+"""C-ABI library: builds, loads without a GPU, exports what the header declares.
+
+No compute calls here (no GPU on the CPU runner).
+"""
+import ctypes
+import os
+import subprocess
+import textwrap
+
+import pytest
+
+from paper_2311_10048_gb300 import lno_ot
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_header_function(lib):
+    names = lno_ot.exported_names()
+    assert {"lno_ot_init", "lno_ot_energy", "lno_ot_energy_batched", "lno_ot_backward",
+            "lno_ot_destroy", "lno_ot_strerror"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_strerror_and_version(lib):
+    for code in (0, -1, -2, -3, -4, -5, -6, 99):
+        assert lib.lno_ot_strerror(code)
+    assert lib.lno_ot_version().decode().startswith("lno_ot")
+
+
+def test_null_arguments_rejected_without_device(lib):
+    assert lib.lno_ot_init(None, None) == lno_ot.EINVAL
+    r = lno_ot.Result()
+    assert lib.lno_ot_energy(None, None, ctypes.byref(r)) == lno_ot.EINVAL
+    assert lib.lno_ot_energy_batched(None, 0, None, None) == lno_ot.EINVAL
+    st = lno_ot.Stats()
+    assert lib.lno_ot_last_stats(None, ctypes.byref(st)) == lno_ot.EINVAL
+
+
+def test_ctypes_struct_layouts_match_c(tmp_path):
+    """sizeof/offsetof of every public struct, C compiler vs the binding."""
+    src = tmp_path / "sz.c"
+    src.write_text(textwrap.dedent("""
+        #include <stdio.h>
+        #include <stddef.h>
+        #include "lno_ot.h"
+        int main(void) {
+          printf("%zu %zu %zu %zu %zu\\n", sizeof(lno_ot_options), sizeof(lno_ot_domain),
+                 sizeof(lno_ot_result), sizeof(lno_ot_grad), sizeof(lno_ot_stats));
+          printf("%zu %zu %zu %zu\\n", offsetof(lno_ot_domain, t2ab),
+                 offsetof(lno_ot_domain, e_trip), offsetof(lno_ot_domain, n_sel),
+                 offsetof(lno_ot_stats, elements));
+          return 0;
+        }
+    """))
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = [int(x) for x in out]
+    C = ctypes
+    want = [C.sizeof(lno_ot.Options), C.sizeof(lno_ot.Domain), C.sizeof(lno_ot.Result),
+            C.sizeof(lno_ot.Grad), C.sizeof(lno_ot.Stats),
+            lno_ot.Domain.t2ab.offset, lno_ot.Domain.e_trip.offset, lno_ot.Domain.n_sel.offset,
+            lno_ot.Stats.elements.offset]
+    assert got == want
+
+
+def test_build_is_sm103a_only():
+    from paper_2311_10048_gb300 import build as b
+    assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

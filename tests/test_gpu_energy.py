@@ -1,0 +1,172 @@
+"""GPU path vs the CPU oracle, element by element (per-triplet contributions).
+
+Float64 path: |dE| <= 1e-8 Eh on every case sum and 1e-10 Eh per triplet.
+Tensor-core paths: |dE| <= 1e-7 Eh at the small configuration (BF16X6).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import triples as T
+from paper_2311_10048_gb300 import lno_ot
+from paper_2311_10048_gb300.synth import config_domain, make_domain
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+CASES = ("aaa", "aab", "abb", "bbb")
+
+
+def golden(name):
+    p = os.path.join(GOLD, f"{name}_energy.json")
+    if not os.path.exists(p):
+        pytest.skip(f"stored oracle values {p} not generated")
+    return json.load(open(p))
+
+
+@pytest.fixture(scope="module")
+def ctx64(lib):
+    c = lno_ot.Context(0, "fp64")
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx6(lib):
+    c = lno_ot.Context(0, "bf16x6")
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx3(lib):
+    c = lno_ot.Context(0, "bf16x3")
+    yield c
+    c.close()
+
+
+def run_with_trip(ctx, dom_np, sel=None):
+    dd = lno_ot.to_device(dom_np)
+    na, nb = dd["nocc"]
+    n = [T.n_triplets(c, na, nb) if sel is None or sel[i] is None else len(sel[i])
+         for i, c in enumerate(CASES)]
+    et = [torch.zeros(max(k, 1), dtype=torch.float64, device="cuda") for k in n]
+    out = ctx.energy(dd, e_trip=et, trip_sel=sel)
+    return out, [e[:k].cpu().numpy() for e, k in zip(et, n)]
+
+
+def test_c0_fp64_per_triplet_matches_stored_oracle(ctx64):
+    g = golden("c0")
+    out, et = run_with_trip(ctx64, config_domain("c0"))
+    for i, c in enumerate(CASES):
+        ref = np.array(g["cases"][c]["e"])
+        assert et[i].shape == ref.shape
+        assert np.abs(et[i] - ref).max() <= 1e-10, c
+        assert abs(out[c] - g["cases"][c]["sum"]) <= 1e-8, c
+    assert abs(out["total"] - g["total"]) <= 1e-8
+
+
+SHAPES = [  # nbas, na, nb, naux, seed -- ragged tiles, tiny and degenerate spaces
+    (7, 3, 2, 14, 1), (9, 3, 3, 20, 2), (20, 5, 1, 40, 3), (37, 4, 3, 70, 4),
+    (50, 7, 4, 90, 5), (23, 6, 6, 46, 6), (18, 3, 0, 30, 7), (40, 2, 1, 64, 8),
+    (33, 16, 14, 48, 9),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_shapes_fp64_vs_oracle(ctx64, shape):
+    nbas, na, nb, naux, seed = shape
+    d = make_domain(nbas, (na, nb), naux=naux, L=naux / 3, seed=seed, t1_sd=0.02)
+    out, et = run_with_trip(ctx64, d)
+    ev = T.Evaluator(d)
+    for i, c in enumerate(CASES):
+        ref = [float(ev.triplet_energy(c, t)) for t in T.triplets(c, na, nb)]
+        if ref:
+            assert np.abs(et[i] - np.array(ref)).max() <= 1e-11 * max(1.0, np.abs(ref).max()), c
+        assert abs(out[c] - math.fsum(ref)) <= 1e-9 * max(1.0, abs(out[c])), c
+
+
+def test_no_virtuals_and_no_triplets(ctx64):
+    d = make_domain(5, (5, 3), naux=10, L=4.0, seed=11)   # spin up has no virtual
+    out = ctx64.energy(lno_ot.to_device(d))
+    ref = T.energy(d)
+    for c in CASES:
+        assert abs(out[c] - ref[c]) <= 1e-12
+    d = make_domain(12, (2, 1), naux=20, L=6.0, seed=12)  # aaa, bbb, abb empty
+    out = ctx64.energy(lno_ot.to_device(d))
+    assert out["aaa"] == 0.0 and out["bbb"] == 0.0 and out["abb"] == 0.0
+    assert abs(out["aab"] - T.energy(d)["aab"]) <= 1e-12
+
+
+def test_triplet_subset(ctx64):
+    d = config_domain("c0")
+    g = golden("c0")
+    sel = [np.array([0, 5, 19]), np.array([59, 1, 30]), None, np.array([3])]
+    out, et = run_with_trip(ctx64, d, sel)
+    for i, c in enumerate(CASES):
+        ref = np.array(g["cases"][c]["e"])
+        want = ref if sel[i] is None else ref[sel[i]]
+        assert np.abs(et[i] - want).max() <= 1e-10
+        assert abs(out[c] - math.fsum(want)) <= 1e-9
+
+
+def test_c0_bf16x6_within_1e7(ctx6):
+    g = golden("c0")
+    out, et = run_with_trip(ctx6, config_domain("c0"))
+    for i, c in enumerate(CASES):
+        assert abs(out[c] - g["cases"][c]["sum"]) <= 1e-7, (c, out[c], g["cases"][c]["sum"])
+    assert abs(out["total"] - g["total"]) <= 1e-7
+
+
+def test_c0_bf16x3_close(ctx3):
+    g = golden("c0")
+    out, _ = run_with_trip(ctx3, config_domain("c0"))
+    assert abs(out["total"] - g["total"]) <= 1e-4 * abs(g["total"])
+
+
+@pytest.mark.parametrize("shape", SHAPES[:5])
+def test_shapes_bf16x6_vs_oracle(ctx6, shape):
+    nbas, na, nb, naux, seed = shape
+    d = make_domain(nbas, (na, nb), naux=naux, L=naux / 3, seed=seed, t1_sd=0.02)
+    out, _ = run_with_trip(ctx6, d)
+    ref = T.energy(d)
+    for c in CASES:
+        assert abs(out[c] - ref[c]) <= 1e-7 + 1e-7 * abs(ref[c]), c
+
+
+def test_error_codes(ctx64, lib):
+    import ctypes
+    d = config_domain("c0")
+    dd = lno_ot.to_device(d)
+    s, keep = lno_ot.make_domain_struct(dd)
+    s.nocc[1] = s.nocc[0] + 1
+    assert ctx64.energy_raw(s)[0] == lno_ot.EINVAL
+    s, keep = lno_ot.make_domain_struct(dd)
+    s.B[0] = None
+    assert ctx64.energy_raw(s)[0] == lno_ot.EINVAL
+    host = torch.zeros(10, dtype=torch.float64)
+    s, keep = lno_ot.make_domain_struct(dd)
+    s.eps[1] = host.data_ptr()
+    assert ctx64.energy_raw(s)[0] == lno_ot.EDEVICE
+    s, keep = lno_ot.make_domain_struct(dd)
+    s.fov[0] = dd["eps"][0].data_ptr()
+    assert ctx64.energy_raw(s)[0] == lno_ot.EUNSUPPORTED
+    s, keep = lno_ot.make_domain_struct(dd, trip_sel=[np.array([10 ** 6]), None, None, None])
+    assert ctx64.energy_raw(s)[0] == lno_ot.EINVAL
+    with pytest.raises(lno_ot.LnoError):
+        lno_ot.Context(0, "tf32").energy(dd)
+    # the context stays usable after errors
+    assert abs(ctx64.energy(dd)["total"] - golden("c0")["total"]) <= 1e-8
+
+
+def test_c4_fp64_matches_stored_oracle(ctx64):
+    g = golden("c4")
+    out, et = run_with_trip(ctx64, config_domain("c4"))
+    for i, c in enumerate(CASES):
+        ref = np.array(g["cases"][c]["e"])
+        assert np.abs(et[i] - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max()), c
+        assert abs(out[c] - g["cases"][c]["sum"]) <= 1e-8, c
+    assert abs(out["total"] - g["total"]) <= 1e-8
