@@ -356,15 +356,37 @@ __device__ __forceinline__ TwoF df_sub(TwoF a, TwoF b) {
   return {h, __fsub_rn(e, __fsub_rn(h, s))};
 }
 
+// q ~ num / D: hardware reciprocal refined by one Newton step (its error is
+// then ~2^-46, i.e. the bias of the approximation is gone), times num with
+// one round-to-nearest.  |D| >= 0.8 Eh here (occupied < 0 < virtual).
+__device__ __forceinline__ float div_nr(float num, float D) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(D));
+  const float e = __fmaf_rn(-D, r, 1.0f);
+  r = __fmaf_rn(r, e, r);
+  return __fmul_rn(num, r);
+}
+
 // Energy of float32 X with register prefetch of the next cube tile.
+// Shared layout per tile (thread (b,c) loops over a):
+//   T1[b][c][a] rows of 20 floats (16-byte aligned: read as float4)
+//   T2[a][c][b], T3[a][b][c] rows of 17 floats (conflict-free scalar reads)
+//   ad[a]   = {t1 of the triplet's occupied on a (up to 3), eps_a hi}, ael[a] = eps_a lo
+//   kac[a][c], kab[a][b]: float4 of the V-table planes on (A,C) and (A,B)
 template <bool MIXED>
 __global__ void __launch_bounds__(256, 2)
 energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ Z,
            const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt) {
-  __shared__ float T1[TB * TB * TP], T2[TB * TB * TP], T3[TB * TB * TP];
-  __shared__ float vt[9][TB][TP];
-  __shared__ float t1s[9][TB];
-  __shared__ float eh[3][TB], el[3][TB];
+  constexpr int P1 = 20;
+  __shared__ __align__(16) float T1[TB * TB * P1];
+  __shared__ float T2[TB * TB * TP], T3[TB * TB * TP];
+  __shared__ __align__(16) float4 kac[TB][TB];
+  __shared__ __align__(16) float4 kab[TB][TB];
+  __shared__ float kbc[3][TB][TP];
+  __shared__ __align__(16) float4 ad[TB];
+  __shared__ float ael[TB];
+  __shared__ float tb_s[3][TB], tc_s[3][TB];
+  __shared__ float ebh[2][TB], ebl[2][TB];
   __shared__ double red[8];
 
   const int g = blockIdx.y;
@@ -417,7 +439,6 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
       if (ok2) xr[1][u] = __ldg(p2 + u);
       if (ok3) xr[2][u] = __ldg(p3 + u);
     }
-    // V tables: plane element (r1, r2)
     if (!MIXED) {
       const int rows[3] = {b0, a0, a0}, cols[3] = {c0, c0, b0};
 #pragma unroll
@@ -473,25 +494,35 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
     const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
     // ---- registers -> shared ----
     {
-      float* d1 = T1 + (r1 * TB + r2) * TP;
+      float4* d1 = reinterpret_cast<float4*>(T1 + (r1 * TB + r2) * P1);
       float* d2 = T2 + (r1 * TB + r2) * TP;
       float* d3 = T3 + (r1 * TB + r2) * TP;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (ok1) { d1[4 * u] = xr[0][u].x; d1[4 * u + 1] = xr[0][u].y; d1[4 * u + 2] = xr[0][u].z; d1[4 * u + 3] = xr[0][u].w; }
+        if (ok1) d1[u] = xr[0][u];
         if (ok2) { d2[4 * u] = xr[1][u].x; d2[4 * u + 1] = xr[1][u].y; d2[4 * u + 2] = xr[1][u].z; d2[4 * u + 3] = xr[1][u].w; }
         if (ok3) { d3[4 * u] = xr[2][u].x; d3[4 * u + 1] = xr[2][u].y; d3[4 * u + 2] = xr[2][u].z; d3[4 * u + 3] = xr[2][u].w; }
       }
-#pragma unroll
-      for (int k = 0; k < 9; ++k)
-        if (!MIXED || k < 5) vt[k][r1][r2] = vr[k];
+      if (!MIXED) {
+        kbc[0][r1][r2] = vr[0]; kbc[1][r1][r2] = vr[1]; kbc[2][r1][r2] = vr[2];
+        kac[r1][r2] = make_float4(vr[3], vr[4], vr[5], 0.f);
+        kab[r1][r2] = make_float4(vr[6], vr[7], vr[8], 0.f);
+      } else {
+        kbc[0][r1][r2] = vr[0]; kbc[1][r1][r2] = vr[1];
+        kac[r1][r2] = make_float4(vr[2], vr[3], 0.f, 0.f);
+        kab[r1][r2] = make_float4(vr[4], 0.f, 0.f, 0.f);
+      }
       if (tid < 3 * TB) {
         const int bl = tid / TB, l = tid % TB;
-        t1s[bl * 3 + 0][l] = t1r[0];
-        t1s[bl * 3 + 1][l] = t1r[1];
-        t1s[bl * 3 + 2][l] = t1r[2];
-        eh[bl][l] = er.hi;
-        el[bl][l] = er.lo;
+        if (bl == 0) {
+          ad[l] = make_float4(t1r[0], t1r[1], t1r[2], er.hi);
+          ael[l] = er.lo;
+        } else {
+          float* tt = bl == 1 ? &tb_s[0][0] : &tc_s[0][0];
+          tt[l] = t1r[0]; tt[TB + l] = t1r[1]; tt[2 * TB + l] = t1r[2];
+          ebh[bl - 1][l] = er.hi;
+          ebl[bl - 1][l] = er.lo;
+        }
       }
     }
     __syncthreads();
@@ -502,38 +533,41 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
       const int b = b0 + bl, c = c0 + cl;
       const bool rowok = MIXED ? (b < nvs && c < nvt) : (b < c && c < nvs);
       if (rowok) {
-        const TwoF dbc = df_sub(df_sub(eocc, TwoF{eh[1][bl], el[1][bl]}), TwoF{eh[2][cl], el[2][cl]});
+        const TwoF dbc = df_sub(df_sub(eocc, TwoF{ebh[0][bl], ebl[0][bl]}), TwoF{ebh[1][cl], ebl[1][cl]});
         const int na = min(b, a0 + TB) - a0;
-        const float* x1p = T1 + (bl * TB + cl) * TP;
+        const float4* x1v = reinterpret_cast<const float4*>(T1 + (bl * TB + cl) * P1);
+        const float* x2p = T2 + cl * TP + bl;
+        const float* x3p = T3 + bl * TP + cl;
         float part = 0.f;
-        if (!MIXED) {
-          const float k0 = vt[0][bl][cl], k1 = vt[1][bl][cl], k2 = vt[2][bl][cl];
-          const float tb0 = t1s[3][bl], tb1 = t1s[4][bl], tb2 = t1s[5][bl];
-          const float tc0 = t1s[6][cl], tc1 = t1s[7][cl], tc2 = t1s[8][cl];
-          for (int al = 0; al < na; ++al) {
-            const float w = x1p[al] - T2[(al * TB + cl) * TP + bl] + T3[(al * TB + bl) * TP + cl];
-            const float ya = t1s[0][al] * k0 + t1s[1][al] * k1 + t1s[2][al] * k2;
-            const float yb = tb0 * vt[3][al][cl] + tb1 * vt[4][al][cl] + tb2 * vt[5][al][cl];
-            const float yc = tc0 * vt[6][al][bl] + tc1 * vt[7][al][bl] + tc2 * vt[8][al][bl];
-            const float v = ya - yb + yc;
-            const float num = __fmul_rn(w, __fadd_rn(w, v));
-            float s, e;
-            two_sum(dbc.hi, -eh[0][al], s, e);
-            const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc.lo, el[0][al])));
-            part = __fadd_rn(part, __fdiv_rn(num, D));
-          }
-        } else {
-          const float mjb = vt[0][bl][cl], mib = vt[1][bl][cl];
-          const float tbi = t1s[3][bl], tbj = t1s[4][bl], tC = t1s[6][cl];
-          for (int al = 0; al < na; ++al) {
-            const float w = x1p[al] - T2[(al * TB + cl) * TP + bl] + T3[(al * TB + bl) * TP + cl];
-            const float v = t1s[0][al] * mjb - t1s[1][al] * mib - tbi * vt[2][al][cl] +
-                            tbj * vt[3][al][cl] + tC * vt[4][al][bl];
-            const float num = __fmul_rn(w, __fadd_rn(w, v));
-            float s, e;
-            two_sum(dbc.hi, -eh[0][al], s, e);
-            const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc.lo, el[0][al])));
-            part = __fadd_rn(part, __fdiv_rn(num, D));
+        const float k0 = kbc[0][bl][cl], k1 = kbc[1][bl][cl], k2 = kbc[2][bl][cl];
+        const float tb0 = tb_s[0][bl], tb1 = tb_s[1][bl], tb2 = tb_s[2][bl];
+        const float tc0 = tc_s[0][cl], tc1 = tc_s[1][cl], tc2 = tc_s[2][cl];
+        for (int a4 = 0; a4 < na; a4 += 4) {
+          const float4 x1q = x1v[a4 >> 2];
+          const float x1a[4] = {x1q.x, x1q.y, x1q.z, x1q.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int al = a4 + u;
+            if (al < na) {
+              const float w = x1a[u] - x2p[al * (TB * TP)] + x3p[al * (TB * TP)];
+              const float4 da = ad[al];
+              const float4 vac = kac[al][cl];
+              const float4 vab = kab[al][bl];
+              float v;
+              if (!MIXED) {
+                const float ya = da.x * k0 + da.y * k1 + da.z * k2;
+                const float yb = tb0 * vac.x + tb1 * vac.y + tb2 * vac.z;
+                const float yc = tc0 * vab.x + tc1 * vab.y + tc2 * vab.z;
+                v = ya - yb + yc;
+              } else {
+                v = da.x * k0 - da.y * k1 - tb0 * vac.x + tb1 * vac.y + tc0 * vab.x;
+              }
+              const float num = __fmul_rn(w, __fadd_rn(w, v));
+              float s, e;
+              two_sum(dbc.hi, -da.w, s, e);
+              const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc.lo, ael[al])));
+              part = __fadd_rn(part, div_nr(num, D));
+            }
           }
         }
         float s, e;
