@@ -193,6 +193,22 @@ LNO_OT_API const char* lno_ot_strerror(int code);
 LNO_OT_API int lno_ot_selftest_gemm(int device, int S, int M, int N, int K, const double* A,
                                     const double* B, double* C, void* stream);
 
+/* The same product as lno_ot_selftest_gemm (same slicing, same kernel, same
+ * result) for callers that must not allocate device memory: programs whose
+ * HBM is owned by their own pool or arena, or code paths where a cudaMalloc
+ * would synchronise the device or is not permitted.  No counterpart in the
+ * paper.  It calls no cudaMalloc/cudaFree or allocating library routine; its
+ * scratch is one static device array of 64 MiB held by every GPU that loads
+ * the library.  Operands must fit: 256 B + sum over A and B of
+ * S * ceil8(rows * ceil8(K)) * 2 bytes (each part rounded up to 256 B)
+ * <= 64 MiB, else LNO_OT_EINVAL (lno_ot_last_error() says how much is needed).
+ * The first call on a device looks up the array's address (make it before
+ * any stream capture).  Every call reuses the array and clears what must
+ * start at zero; calls that overlap on the GPU race on it.  Synchronous on
+ * `stream` (NULL = legacy default stream). */
+LNO_OT_API int lno_ot_gemm_sliced_noalloc(int device, int S, int M, int N, int K, const double* A,
+                                          const double* B, double* C, void* stream);
+
 /* Text of the last CUDA failure seen by this host thread ("" if none). */
 LNO_OT_API const char* lno_ot_last_error(void);
 
