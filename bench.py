@@ -208,13 +208,19 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c1", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="c1", choices=sorted(CONFIGS) + ["custom"])
     ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x3"])
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle triplets per case")
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--fp64-sample", type=int, default=2, help="FP64-path triplets per case")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--shape", default=None,
+                    help="custom domain nbas,nalpha,nbeta,naux (recipe of the configs, seed 5)")
     args = ap.parse_args()
+    if args.shape:
+        nbas_, na_, nb_, naux_ = (int(x) for x in args.shape.split(","))
+        CONFIGS["custom"] = dict(nbas=nbas_, nocc=(na_, nb_), naux=naux_, L=naux_ / 4.0, seed=5)
+        args.config = "custom"
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

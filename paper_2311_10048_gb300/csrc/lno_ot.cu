@@ -14,6 +14,7 @@
 // BF16X3 / BF16X6 precisions run them on the tensor cores on exact BF16
 // slices (tc_gemm.cu), with float64 kept for orbital energies and sums.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -68,6 +69,11 @@ template <int S, int BN, typename OutT>
 cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
                            int nprob, int M, int N, int ldo, double scale, int* flag,
                            unsigned long long* amax, int nsm, cudaStream_t st);
+template <int S, int BN, typename OutT>
+cudaError_t launch_tc_gemm_mc(const CUtensorMap* mA64, const CUtensorMap* mB,
+                              const TcProb* probs_dev, int nprob, int M, int N, int ldo,
+                              double scale, int* flag, unsigned long long* amax, int nsm,
+                              cudaStream_t st);
 }  // namespace lno
 
 using namespace lno;
@@ -88,6 +94,7 @@ struct lno_ot_ctx {
   bool own_stream = false;
   size_t ws_limit = 0;
   int nsm = 152;
+  bool cluster = true;                 // W contractions in 2-CTA multicast clusters
   int* d_flag = nullptr;               // device error flag (bounded waits)
   unsigned long long* d_amax = nullptr;
   double* d_sums = nullptr;            // [8]
@@ -170,7 +177,7 @@ struct Operand {
   __nv_bfloat16* bf = nullptr;
   int S = 0;
   int64_t slice_stride = 0;
-  CUtensorMap mapA, mapB, mapB128;  // box rows: 128 (A role), 256 / 128 (B role)
+  CUtensorMap mapA, mapA64, mapB, mapB128;  // box rows: 128 / 64 (A role), 256 / 128 (B role)
   int64_t total_rows() const { return (int64_t)nslot * rows; }
 };
 
@@ -226,6 +233,8 @@ struct Run {
                            op.slice_stride, 256));
       TRY(make_operand_map(&op.mapB128, op.bf, op.Kp, std::max<int64_t>(op.total_rows(), 1),
                            op.S, op.slice_stride, 128));
+      TRY(make_operand_map(&op.mapA64, op.bf, op.Kp, std::max<int64_t>(op.total_rows(), 1), op.S,
+                           op.slice_stride, 64));
     }
     return LNO_OT_OK;
   }
@@ -619,14 +628,25 @@ struct SpinPass {
     } else {
       CU(cudaMemcpyAsync(dpt, pt.data(), nprob * sizeof(TcProb), cudaMemcpyHostToDevice, R.st));
       CUtensorMap mA[2] = {opA0.mapA, opA1.mapA};
+      CUtensorMap mA64[2] = {opA0.mapA64, opA1.mapA64};
       CUtensorMap mB[2] = {R.S == 2 ? opB0.mapB : opB0.mapB128, R.S == 2 ? opB1.mapB : opB1.mapB128};
       const double scale = R.sigT * R.sigI * std::ldexp(1.0, -14);
-      if (R.S == 2)
-        CU(launch_tc_gemm<2, 256, float>(mA, mB, dpt, nprob, M, N, ldo, scale, R.ctx->d_flag,
-                                         nullptr, R.ctx->nsm, R.st));
-      else
-        CU(launch_tc_gemm<3, 128, float>(mA, mB, dpt, nprob, M, N, ldo, scale, R.ctx->d_flag,
-                                         nullptr, R.ctx->nsm, R.st));
+      int* fl = R.ctx->d_flag;
+      const int nsm = R.ctx->nsm;
+      if (R.ctx->cluster) {
+        if (R.S == 2)
+          CU(launch_tc_gemm_mc<2, 256, float>(mA64, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr,
+                                              nsm, R.st));
+        else
+          CU(launch_tc_gemm_mc<3, 128, float>(mA64, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr,
+                                              nsm, R.st));
+      } else if (R.S == 2) {
+        CU(launch_tc_gemm<2, 256, float>(mA, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr, nsm,
+                                         R.st));
+      } else {
+        CU(launch_tc_gemm<3, 128, float>(mA, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr, nsm,
+                                         R.st));
+      }
     }
     if (e1) cudaEventRecord(e1, R.st);
     if (e0 && e1) R.contract_ev.push_back({e0, e1});
@@ -1004,6 +1024,10 @@ int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
   c->prec = opt->precision;
   c->ws_limit = opt->workspace_bytes;
   c->nsm = prop.multiProcessorCount;
+  {  // kernel variant of the W contractions (tuning knob; default: clusters)
+    const char* ev = getenv("LNO_OT_CLUSTER");
+    c->cluster = !(ev && ev[0] == '0');
+  }
   if (opt->stream) {
     c->stream = static_cast<cudaStream_t>(opt->stream);
   } else {

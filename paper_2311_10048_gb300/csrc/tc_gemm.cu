@@ -31,7 +31,9 @@
 //   warp 0      TMA producer (one thread), STAGES-deep smem ring
 //   warp 1      TMEM allocator and MMA issuer (one thread); S accumulators
 //               of 128 x BN FP32 (BN = 256 for S <= 2, 128 for S >= 3)
-//   warps 2..5  epilogue: tcgen05.ld -> scale -> coalesced stores along m
+//   warps 2..5  epilogue: tcgen05.ld -> scale -> coalesced stores along m; when
+//               TMEM has room (S = 3, BN = 128) the combined tile is parked in
+//               spare columns so the next tile's MMAs overlap the stores
 // Every mbarrier wait is bounded; on a timeout the kernel records an error
 // code, drains its own TMA copies and MMAs, frees TMEM and returns.
 #include "common.cuh"
@@ -98,6 +100,28 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Multicast: the box lands at the same CTA-relative offset in every CTA of
+// `mask`, and completes bytes on the barrier at the same offset in each.
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                               int c0, int c1, int c2, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -121,6 +145,14 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
       : "memory");
 }
 
+__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32"
@@ -129,6 +161,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
         "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32"
+      " [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -164,13 +207,18 @@ struct Cfg {
   static_assert(S * BN <= 512, "one TMEM accumulator per weight class");
 };
 
-template <int S, int BN, typename OutT>
+// MC = 1: one CTA per tile.  MC = 2: clusters of two CTAs on adjacent
+// n-tiles of the same m-tile; each loads half of the shared A tile and
+// multicasts it to both (A traffic from L2 halves), and each MMA commit frees
+// the stage in both CTAs (empty barriers count two arrivals).
+template <int S, int BN, typename OutT, int MC>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
                const TcProb* __restrict__ probs, int nprob, int M, int N, int ldo, double scale,
                int* __restrict__ flag, unsigned long long* __restrict__ amax) {
   using C = Cfg<S, BN>;
+  static_assert(MC == 1 || MC == 2, "cluster of one or two CTAs");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -179,8 +227,13 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 3);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = MC == 2 ? cluster_rank() : 0u;
+  const int cid = MC == 2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int ncl = MC == 2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   const int nM = (M + BM - 1) / BM, nN = (N + BN - 1) / BN;
-  const long long ntiles = (long long)nprob * nM * nN;
+  const int nNu = (nN + MC - 1) / MC;            // n-tile units (pairs when MC = 2)
+  const long long nunits = (long long)nprob * nM * nNu;
+  const uint16_t mask = (uint16_t)((1u << MC) - 1u);
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + C::kStages + s); };
   const uint32_t tfull = smem_u32(bars + 2 * C::kStages);
@@ -190,11 +243,18 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
   auto b_addr = [&](int st, int sl) {
     return smem_u32(smem + st * C::kStage + S * C::kABytes + sl * C::kBBytes);
   };
+  // unit -> (problem, m-tile, n-tile of this CTA)
+  auto decode = [&](long long u, int& mt, int& nt, long long& pr) {
+    mt = (int)(u % nM);
+    const long long r = u / nM;
+    nt = (int)(r % nNu) * MC + (int)rank;
+    pr = r / nNu;
+  };
 
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
+      mbar_init(empty_bar(s), MC);
     }
     mbar_init(tfull, 1);
     mbar_init(tempty, 128);
@@ -210,6 +270,7 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (MC == 2) cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -220,11 +281,11 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
       uint32_t phase = 0;
       uint32_t issued_mask = 0, last_phase = 0;
       bool ok = true;
-      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int mt = (int)(t % nM);
-        const long long r = t / nM;
-        const int nt = (int)(r % nN);
-        const TcProb& P = probs[r / nN];
+      for (long long u = cid; u < nunits && ok; u += ncl) {
+        int mt, nt;
+        long long pr;
+        decode(u, mt, nt, pr);
+        const TcProb& P = probs[pr];
         for (int sg = 0; sg < P.nseg && ok; ++sg) {
           const TcSeg seg = P.seg[sg];
           const CUtensorMap* ma = seg.amap ? &mapA1 : &mapA0;
@@ -236,8 +297,14 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
             }
             mbar_expect_tx(full_bar(stage), (uint32_t)C::kStage);
 #pragma unroll
-            for (int sl = 0; sl < S; ++sl)
-              tma_load_3d(a_addr(stage, sl), ma, full_bar(stage), k0, seg.a_row + mt * BM, sl);
+            for (int sl = 0; sl < S; ++sl) {
+              if constexpr (MC == 1) {
+                tma_load_3d(a_addr(stage, sl), ma, full_bar(stage), k0, seg.a_row + mt * BM, sl);
+              } else {  // my half of the A rows, to both CTAs
+                tma_load_3d_mc(a_addr(stage, sl) + rank * (C::kABytes / 2), ma, full_bar(stage), k0,
+                               seg.a_row + mt * BM + (int)rank * (BM / 2), sl, mask);
+              }
+            }
 #pragma unroll
             for (int sl = 0; sl < S; ++sl)
               tma_load_3d(b_addr(stage, sl), mb, full_bar(stage), k0, seg.b_row + nt * BN, sl);
@@ -253,6 +320,12 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
       // every copy this thread issued must have landed before smem goes away
       for (int s = 0; s < C::kStages; ++s)
         if (issued_mask & (1u << s)) mbar_wait(full_bar(s), (last_phase >> s) & 1u, flag, 4, false);
+      if constexpr (MC == 2) {
+        // and every MMA commit of either CTA aimed at this CTA's barriers has arrived
+        for (int s = 0; s < C::kStages; ++s)
+          if (issued_mask & (1u << s))
+            mbar_wait(empty_bar(s), (last_phase >> s) & 1u, flag, 7, false);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -260,8 +333,11 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
       int stage = 0;
       uint32_t phase = 0, tile_it = 0;
       bool ok = true, any = false;
-      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tile_it) {
-        const TcProb& P = probs[(t / nM) / nN];
+      for (long long u = cid; u < nunits && ok; u += ncl, ++tile_it) {
+        int mt, nt;
+        long long pr;
+        decode(u, mt, nt, pr);
+        const TcProb& P = probs[pr];
         if (tile_it > 0 && !mbar_wait(tempty, (tile_it - 1) & 1u, flag, 2, true)) {
           ok = false;
           break;
@@ -294,7 +370,10 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                 }
               }
             }
-            umma_commit(empty_bar(stage));
+            if constexpr (MC == 1)
+              umma_commit(empty_bar(stage));
+            else
+              umma_commit_mc(empty_bar(stage), mask);
             if (++stage == C::kStages) {
               stage = 0;
               phase ^= 1u;
@@ -316,17 +395,56 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     float lmax = 0.f;
     // scale = sigma_A sigma_B 2^-14 is a power of two: exact in float
     const float fscale = (float)scale;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_it) {
-      const int mt = (int)(t % nM);
-      const long long r = t / nM;
-      const int nt = (int)(r % nN);
-      const TcProb& P = probs[r / nN];
+    for (long long u = cid; u < nunits; u += ncl, ++tile_it) {
+      int mt, nt;
+      long long pr;
+      decode(u, mt, nt, pr);
+      const TcProb& P = probs[pr];
       if (!mbar_wait(tfull, tile_it & 1u, flag, 6, true)) break;
       tc_fence_after();
       const int m = mt * BM + row;
       OutT* out = reinterpret_cast<OutT*>(P.out);
       const bool mok = m < M && out != nullptr;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
+      if constexpr ((S + 1) * BN <= 512 && sizeof(OutT) == 4) {
+        // combine the classes into the spare TMEM columns, free the class
+        // accumulators for the next tile's MMAs, then store from the spare copy
+        const uint32_t spare = tbase + S * BN;
+#pragma unroll 1
+        for (int c = 0; c < BN / 16; ++c) {
+          uint32_t acc[S][16];
+#pragma unroll
+          for (int g = 0; g < S; ++g) tmem_ld16(tbase + g * BN + c * 16, acc[g]);
+          tmem_ld_wait();
+          uint32_t v[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float lo = 0.f;
+#pragma unroll
+            for (int g = S - 1; g >= 1; --g) lo = __fadd_rn(lo, __uint_as_float(acc[g][j]));
+            v[j] = __float_as_uint(__fmul_rn(__fadd_rn(__uint_as_float(acc[0][j]), lo), fscale));
+          }
+          tmem_st16(spare + c * 16, v);
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(tempty);
+#pragma unroll 1
+        for (int c = 0; c < BN / 16; ++c) {
+          uint32_t v[16];
+          tmem_ld16(spare + c * 16, v);
+          tmem_ld_wait();
+          const int n0 = nt * BN + c * 16;
+          OutT* op = out + (int64_t)n0 * ldo + m;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float x = __uint_as_float(v[j]);
+            if (mok && n0 + j < N) op[(int64_t)j * ldo] = x;
+            if (amax != nullptr && m < M && n0 + j < N) lmax = fmaxf(lmax, fabsf(x));
+          }
+        }
+        continue;
+      }
 #pragma unroll 1
       for (int c = 0; c < BN / 16; ++c) {
         uint32_t acc[S][16];
@@ -367,6 +485,7 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
                  : "memory");
   }
+  if constexpr (MC == 2) cluster_sync();  // neither CTA leaves while the other may still signal it
 }
 
 }  // namespace
@@ -413,7 +532,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const T
                            unsigned long long* amax, int nsm, cudaStream_t st) {
   using C = Cfg<S, BN>;
   if (nprob <= 0 || M <= 0 || N <= 0) return cudaSuccess;
-  auto k = tc_gemm_sliced<S, BN, OutT>;
+  auto k = tc_gemm_sliced<S, BN, OutT, 1>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   if (e != cudaSuccess) return e;
   const long long ntiles = (long long)nprob * ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
@@ -423,7 +542,56 @@ cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const T
   return cudaGetLastError();
 }
 
+// Clusters of two CTAs sharing the A tile by TMA multicast.  The A maps must
+// have boxes of 64 rows (half a tile).
+template <int S, int BN, typename OutT>
+cudaError_t launch_tc_gemm_mc(const CUtensorMap* mA64, const CUtensorMap* mB,
+                              const TcProb* probs_dev, int nprob, int M, int N, int ldo,
+                              double scale, int* flag, unsigned long long* amax, int nsm,
+                              cudaStream_t st) {
+  using C = Cfg<S, BN>;
+  if (nprob <= 0 || M <= 0 || N <= 0) return cudaSuccess;
+  auto k = tc_gemm_sliced<S, BN, OutT, 2>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(192, 1, 1);
+  cfg.dynamicSmemBytes = C::kSmem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  static int max_clusters = 0;
+  if (max_clusters == 0) {
+    cfg.gridDim = dim3(2 * (nsm / 2), 1, 1);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = nsm / 2;
+    }
+    max_clusters = n;
+  }
+  const long long nunits = (long long)nprob * ((M + BM - 1) / BM) * (((N + BN - 1) / BN + 1) / 2);
+  const int ncl = (int)(nunits < max_clusters ? nunits : max_clusters);
+  cfg.gridDim = dim3(2 * ncl, 1, 1);
+  e = cudaLaunchKernelEx(&cfg, k, mA64[0], mA64[1], mB[0], mB[1], probs_dev, nprob, M, N, ldo,
+                         scale, flag, amax);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 int tc_products(int S) { return S * (S + 1) / 2; }
+
+template cudaError_t launch_tc_gemm_mc<2, 256, float>(const CUtensorMap*, const CUtensorMap*,
+                                                      const TcProb*, int, int, int, int, double,
+                                                      int*, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_tc_gemm_mc<3, 128, float>(const CUtensorMap*, const CUtensorMap*,
+                                                      const TcProb*, int, int, int, int, double,
+                                                      int*, unsigned long long*, int, cudaStream_t);
 
 template cudaError_t launch_tc_gemm<2, 256, float>(const CUtensorMap*, const CUtensorMap*,
                                                    const TcProb*, int, int, int, int, double, int*,
