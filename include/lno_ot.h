@@ -76,7 +76,7 @@ typedef struct {
   int device;             /* CUDA device ordinal */
   int precision;          /* lno_ot_precision */
   void* stream;           /* cudaStream_t to order all work on; NULL = the
-                             library creates and owns a non-blocking stream */
+                             legacy default stream */
   size_t workspace_bytes; /* upper bound on device workspace; 0 = no bound */
   const char* tune_cache; /* reserved, may be NULL */
 } lno_ot_options;
@@ -160,7 +160,7 @@ typedef struct {
 /* Create a context on opt->device.  *ctx is set only on success. */
 LNO_OT_API int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt);
 
-/* Release the context, its workspace and the stream it created (if any). */
+/* Release the context and its device buffers (after its stream drained). */
 LNO_OT_API void lno_ot_destroy(lno_ot_ctx* ctx);
 
 /* E(T) of one domain (eq cim_pt_energy, all occupied orbitals of the

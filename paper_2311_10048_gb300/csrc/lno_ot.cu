@@ -74,6 +74,41 @@ cudaError_t launch_tc_gemm_mc(const CUtensorMap* mA64, const CUtensorMap* mB,
                               const TcProb* probs_dev, int nprob, int M, int N, int ldo,
                               double scale, int* flag, unsigned long long* amax, int nsm,
                               cudaStream_t st);
+// backward.cu
+struct GemmS {
+  const double* A;
+  const double* B;
+  double* C;
+  int M, N, K;
+  int atomic;
+  int64_t sam, sak, sbk, sbn, scm, scn;
+  double alpha;
+};
+cudaError_t launch_gemm_strided(const GemmS* probs_dev, int nprob, int maxM, int maxN,
+                                cudaStream_t st);
+cudaError_t launch_energy_backward(const EnergyArgs& a, const double* X, const double* Z,
+                                   double* dX, double* dZ, double* dt1s, double* dt1t,
+                                   double* dov_ss, double* dov_ts, double* deps_s,
+                                   double* deps_t, double gscale, int ntrip, int nchunks,
+                                   cudaStream_t st);
+cudaError_t launch_adj_at_same(const int2*, int, int, int, int, const double*, double*, double*,
+                               cudaStream_t);
+cudaError_t launch_adj_bt_same(int, int, int, int, int, const double*, double*, double*,
+                               cudaStream_t);
+cudaError_t launch_adj_a1(const int2*, int, int, int, int, int, int, const double*, double*,
+                          double*, cudaStream_t);
+cudaError_t launch_adj_bg(int, int, int, int, int, int, int, const double*, double*, double*,
+                          cudaStream_t);
+cudaError_t launch_adj_bf(int, int, int, int, int, int, int, const double*, double*, double*,
+                          cudaStream_t);
+cudaError_t launch_adj_at2(const int2*, int, int, int, int, int, int, const double*, double*,
+                           double*, cudaStream_t);
+cudaError_t launch_adj_transpose_block(const double*, int, int, int, int, int, int, int, double*,
+                                       cudaStream_t);
+cudaError_t launch_sym_project(const double*, int, int, double, double*, cudaStream_t);
+cudaError_t launch_antisym_project(const double*, int, int, double, double*, cudaStream_t);
+cudaError_t launch_adj_transpose_t2ab(const double*, int, int, int, int, double*, cudaStream_t);
+cudaError_t launch_scale_copy(const double*, int64_t, double, double*, cudaStream_t);
 }  // namespace lno
 
 using namespace lno;
@@ -1000,6 +1035,391 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
   return LNO_OT_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Adjoint (float64).  Gradient accumulators of one domain (raw, unprojected).
+struct GradAcc {
+  Operand dBoo[2], dBov[2], dBvv[2];  // same layout as the DF blocks
+  double* dovov_ss[2];
+  double* dt1[2];
+  double* deps[2];
+  double* dt2aa;
+  double* dt2bb;
+  double* dt2ab;
+};
+
+int zeros(Arena& A, double** p, int64_t n, cudaStream_t st) {
+  TRY(A.get(p, (size_t)std::max<int64_t>(n, 1)));
+  CU(cudaMemsetAsync(*p, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(double), st));
+  return LNO_OT_OK;
+}
+
+int zero_operand_like(Arena& A, const Operand& src, Operand& d, cudaStream_t st) {
+  d = src;
+  const int64_t n = std::max<int64_t>((int64_t)src.nslot * src.rows * src.Kp, 8);
+  return zeros(A, &d.f64, n, st);
+}
+
+// DF adjoint: out[n][m] = sum_Q L[l0+m][Q] R[r0+n][Q]  ->  dL, dR (+=)
+int df_adjoint(Run& R, Arena& A, const Operand& Lo, Operand& dL, int64_t l0, int M,
+               const Operand& Ro, Operand& dR, int64_t r0, int N, const double* dout, int ldo) {
+  if (M <= 0 || N <= 0) return LNO_OT_OK;
+  GemmS g[2];
+  const int64_t Qp = Lo.Kp;
+  g[0] = GemmS{dout, Ro.f64 + r0 * Qp, dL.f64 + l0 * Qp, M, R.naux, N, 0,
+               1, ldo, Qp, 1, Qp, 1, 1.0};
+  g[1] = GemmS{dout, Lo.f64 + l0 * Qp, dR.f64 + r0 * Qp, N, R.naux, M, 0,
+               ldo, 1, Qp, 1, Qp, 1, 1.0};
+  GemmS* dg;
+  TRY(A.get(&dg, 2));
+  CU(cudaMemcpyAsync(dg, g, sizeof g, cudaMemcpyHostToDevice, R.st));
+  CU(launch_gemm_strided(dg, 1, M, R.naux, R.st));
+  CU(launch_gemm_strided(dg + 1, 1, N, R.naux, R.st));
+  R.stats->other_launches += 2;
+  CU(cudaStreamSynchronize(R.st));  // g lives on the host stack
+  A.drop(dg);
+  return LNO_OT_OK;
+}
+
+int backward_spin(SpinPass& P, GradAcc& G, double gE) {
+  Run& R = P.R;
+  cudaStream_t st = R.st;
+  Arena A(st, 0);
+  const int o = P.o, v = P.v, ot = P.ot, vt = P.vt, s = P.s, t = P.t;
+  Operand dAT, dBT, dA1, dBG, dBF, dAT2;
+  TRY(zero_operand_like(A, P.AT, dAT, st));
+  TRY(zero_operand_like(A, P.BT, dBT, st));
+  TRY(zero_operand_like(A, P.A1, dA1, st));
+  TRY(zero_operand_like(A, P.BG, dBG, st));
+  TRY(zero_operand_like(A, P.BF, dBF, st));
+  TRY(zero_operand_like(A, P.AT2, dAT2, st));
+  double* dovov_ts = nullptr;
+  if (!P.mixed.trips.empty()) TRY(zeros(A, &dovov_ts, (int64_t)o * v * ot * vt, st));
+  double* dt2ss = s == 0 ? G.dt2aa : G.dt2bb;
+  double* dt2st = G.dt2ab;
+  if (s == 1 && !P.mixed.trips.empty()) TRY(zeros(A, &dt2st, (int64_t)o * ot * v * vt, st));
+
+  // ---- per case: recompute, energy adjoint, contraction adjoint ------------
+  for (int im = 0; im < 2; ++im) {
+    const bool is_mixed = im == 1;
+    CaseSel& cs = is_mixed ? P.mixed : P.same;
+    const int ntrip = (int)cs.trips.size();
+    if (ntrip == 0) continue;
+    if (v == 0 || (is_mixed && vt == 0)) continue;
+    const int M1 = v;
+    const int64_t N1 = is_mixed ? (int64_t)v * vt : npairs(v);
+    const int P1 = (int)round_up(std::max(M1, 1), 16);
+    const int M2 = vt;
+    const int64_t N2 = is_mixed ? npairs(v) : 0;
+    const int P2 = (int)round_up(std::max(M2, 1), 16);
+    const int64_t per = (N1 * P1 + N2 * P2) * 8 * 2;
+    int Gn = (int)std::max<int64_t>(1, std::min<int64_t>(32, ((int64_t)4 << 30) / std::max<int64_t>(per, 1)));
+    Gn = std::min(Gn, ntrip);
+    double *X, *Z = nullptr, *dX, *dZ = nullptr;
+    TRY(A.get(&X, (size_t)(Gn * N1 * P1) + 8));
+    TRY(A.get(&dX, (size_t)(Gn * N1 * P1) + 8));
+    if (is_mixed) {
+      TRY(A.get(&Z, (size_t)(Gn * N2 * P2) + 8));
+      TRY(A.get(&dZ, (size_t)(Gn * N2 * P2) + 8));
+    }
+    std::vector<int3> blocks;
+    const int nbs = (v + 15) / 16, nbt = (vt + 15) / 16;
+    for (int a = 0; a < nbs; ++a)
+      for (int b = a; b < nbs; ++b)
+        if (!is_mixed) {
+          for (int c = b; c < nbs; ++c) blocks.push_back(make_int3(a, b, c));
+        } else {
+          for (int c = 0; c < nbt; ++c) blocks.push_back(make_int3(a, b, c));
+        }
+    int3* dblocks;
+    TRY(A.get(&dblocks, blocks.size()));
+    CU(cudaMemcpyAsync(dblocks, blocks.data(), blocks.size() * sizeof(int3),
+                       cudaMemcpyHostToDevice, st));
+    Trip* dtrips;
+    TRY(A.get(&dtrips, (size_t)ntrip));
+    CU(cudaMemcpyAsync(dtrips, cs.trips.data(), ntrip * sizeof(Trip), cudaMemcpyHostToDevice,
+                       st));
+    const int Pch = std::max(1, std::min((int)blocks.size(), R.ctx->nsm * 4 / Gn + 1));
+    EnergyArgs ea{};
+    ea.kind = is_mixed ? MIXED : SAME;
+    ea.nvs = v;
+    ea.nvt = is_mixed ? vt : v;
+    ea.nos = o;
+    ea.not_ = is_mixed ? ot : o;
+    ea.eps_s = R.dom->eps[s];
+    ea.eps_t = R.dom->eps[is_mixed ? t : s];
+    ea.t1s = R.dom->t1[s];
+    ea.t1t = R.dom->t1[is_mixed ? t : s];
+    ea.ovov_ss = R.ovov_ss[s];
+    ea.ovov_ts = P.ovov_ts;
+    ea.blocks = dblocks;
+    ea.nblocks = (int)blocks.size();
+    ea.pitch_x = P1;
+    ea.pitch_z = P2;
+    ea.x_stride = N1 * P1;
+    ea.z_stride = N2 * P2;
+    ProbF64* dpf;
+    ProbF64* dpf2;
+    GemmS* dgs;
+    TRY(A.get(&dpf, (size_t)Gn));
+    TRY(A.get(&dpf2, (size_t)Gn));
+    TRY(A.get(&dgs, (size_t)Gn * 6));
+    std::vector<ProbF64> pf(Gn), pf2(Gn);
+    struct SegRef {
+      const Operand* A;
+      Operand* dA;
+      int64_t arow;
+      const Operand* B;
+      Operand* dB;
+      int64_t brow;
+      double sign;
+    };
+    for (int g0 = 0; g0 < ntrip; g0 += Gn) {
+      const int ng = std::min(Gn, ntrip - g0);
+      std::vector<std::vector<SegRef>> segs1(ng), segs2(ng);
+      for (int g = 0; g < ng; ++g) {
+        const Trip tr = cs.trips[g0 + g];
+        const int i = tr.i, j = tr.j, k = tr.k;
+        if (!is_mixed) {
+          const int64_t bp = npairs(v);
+          segs1[g] = {{&P.AT, &dAT, (int64_t)P.slotAT[(size_t)j * o + k] * v, &P.BT, &dBT, P.slotBT[i] * bp, 1.0},
+                      {&P.AT, &dAT, (int64_t)P.slotAT[(size_t)k * o + i] * v, &P.BT, &dBT, P.slotBT[j] * bp, 1.0},
+                      {&P.AT, &dAT, (int64_t)P.slotAT[(size_t)i * o + j] * v, &P.BT, &dBT, P.slotBT[k] * bp, 1.0}};
+        } else {
+          const int K = k;
+          const int64_t bp = npairs(v), bgr = (int64_t)v * vt;
+          segs1[g] = {{&P.A1, &dA1, (int64_t)P.slotA1[(size_t)j * ot + K] * v, &P.BG, &dBG, P.slotBG[i] * bgr, 1.0},
+                      {&P.A1, &dA1, (int64_t)P.slotA1[(size_t)i * ot + K] * v, &P.BG, &dBG, P.slotBG[j] * bgr, -1.0},
+                      {&P.AT, &dAT, (int64_t)P.slotAT[(size_t)i * o + j] * v, &P.BF, &dBF, P.slotBF[K] * bgr, 1.0}};
+          segs2[g] = {{&P.AT2, &dAT2, (int64_t)P.slotAT2[(size_t)j * ot + K] * vt, &P.BT, &dBT, P.slotBT[i] * bp, -1.0},
+                      {&P.AT2, &dAT2, (int64_t)P.slotAT2[(size_t)i * ot + K] * vt, &P.BT, &dBT, P.slotBT[j] * bp, 1.0}};
+        }
+        auto fill = [&](ProbF64& pr, const std::vector<SegRef>& sg, double* out) {
+          pr.nseg = (int)sg.size();
+          for (size_t q = 0; q < sg.size(); ++q)
+            pr.seg[q] = SegF64{sg[q].A->f64 + sg[q].arow * sg[q].A->Kp,
+                               sg[q].B->f64 + sg[q].brow * sg[q].B->Kp, sg[q].A->K, sg[q].A->Kp,
+                               sg[q].B->Kp, sg[q].sign};
+          pr.XT = out;
+        };
+        fill(pf[g], segs1[g], X + (size_t)g * N1 * P1);
+        if (is_mixed) fill(pf2[g], segs2[g], Z + (size_t)g * N2 * P2);
+      }
+      // recompute X (and Z')
+      CU(cudaMemcpyAsync(dpf, pf.data(), ng * sizeof(ProbF64), cudaMemcpyHostToDevice, st));
+      CU(launch_gemm_f64(dpf, ng, M1, (int)N1, P1, st));
+      if (is_mixed) {
+        CU(cudaMemcpyAsync(dpf2, pf2.data(), ng * sizeof(ProbF64), cudaMemcpyHostToDevice, st));
+        CU(launch_gemm_f64(dpf2, ng, M2, (int)N2, P2, st));
+      }
+      // energy adjoint -> dX, dT1, deps, V-integral gradients
+      CU(cudaMemsetAsync(dX, 0, (size_t)ng * N1 * P1 * sizeof(double), st));
+      if (is_mixed) CU(cudaMemsetAsync(dZ, 0, (size_t)ng * N2 * P2 * sizeof(double), st));
+      ea.trips = dtrips + g0;
+      CU(launch_energy_backward(ea, X, Z, dX, dZ, G.dt1[s], G.dt1[is_mixed ? t : s], G.dovov_ss[s],
+                                dovov_ts, G.deps[s], G.deps[is_mixed ? t : s], gE, ng, Pch, st));
+      // contraction adjoint: dA += sign dX.B, dB += sign dX^T.A
+      auto adj = [&](const std::vector<std::vector<SegRef>>& segs, const double* dXb, int64_t Nn,
+                     int Mm, int ldo) -> int {
+        for (int q = 0; q < 3; ++q) {  // one launch per segment position
+          std::vector<GemmS> ga, gb;
+          int maxKa = 0;
+          for (int g = 0; g < ng; ++g) {
+            if ((int)segs[g].size() <= q) continue;
+            const SegRef& r = segs[g][q];
+            const double* dxg = dXb + (size_t)g * Nn * ldo;
+            const int K = r.A->K;
+            maxKa = std::max(maxKa, K);
+            ga.push_back(GemmS{dxg, r.B->f64 + r.brow * r.B->Kp, r.dA->f64 + r.arow * r.A->Kp,
+                               Mm, K, (int)Nn, 1, 1, ldo, r.B->Kp, 1, r.A->Kp, 1, r.sign});
+            gb.push_back(GemmS{dxg, r.A->f64 + r.arow * r.A->Kp, r.dB->f64 + r.brow * r.B->Kp,
+                               (int)Nn, K, Mm, 1, ldo, 1, r.A->Kp, 1, r.B->Kp, 1, r.sign});
+          }
+          if (ga.empty()) continue;
+          const int n = (int)ga.size();
+          CU(cudaMemcpyAsync(dgs, ga.data(), n * sizeof(GemmS), cudaMemcpyHostToDevice, st));
+          CU(launch_gemm_strided(dgs, n, Mm, maxKa, st));
+          CU(cudaMemcpyAsync(dgs + Gn * 3, gb.data(), n * sizeof(GemmS), cudaMemcpyHostToDevice,
+                             st));
+          CU(launch_gemm_strided(dgs + Gn * 3, n, (int)Nn, maxKa, st));
+          CU(cudaStreamSynchronize(st));
+        }
+        return LNO_OT_OK;
+      };
+      TRY(adj(segs1, dX, N1, M1, P1));
+      if (is_mixed) TRY(adj(segs2, dZ, N2, M2, P2));
+      CU(cudaStreamSynchronize(st));
+      R.stats->contract_launches += is_mixed ? 2 : 1;
+      R.stats->energy_launches += 1;
+    }
+  }
+
+  // ---- layout adjoints and DF adjoints ---------------------------------------
+  auto upload_pairs = [&](const std::vector<int2>& l, int2** d) -> int {
+    TRY(A.get(d, std::max<size_t>(l.size(), 1)));
+    if (!l.empty())
+      CU(cudaMemcpyAsync(*d, l.data(), l.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    return LNO_OT_OK;
+  };
+  if (!P.listAT.empty()) {
+    double* doovoT;
+    TRY(zeros(A, &doovoT, (int64_t)o * v * o * o, st));
+    int2* dl;
+    TRY(upload_pairs(P.listAT, &dl));
+    CU(launch_adj_at_same(dl, (int)P.listAT.size(), o, v, dAT.Kp, dAT.f64, dt2ss, doovoT, st));
+    TRY(df_adjoint(R, A, R.Boo[s], G.dBoo[s], 0, o * o, R.Bov[s], G.dBov[s], 0, o * v, doovoT,
+                   o * o));
+    A.drop(doovoT);
+  }
+  if (!P.listBT.empty()) {
+    double* dvv;
+    TRY(A.get(&dvv, (size_t)v * v * v));
+    for (size_t q = 0; q < P.listBT.size(); ++q) {
+      const int x = P.listBT[q];
+      CU(cudaMemsetAsync(dvv, 0, (size_t)v * v * v * sizeof(double), st));
+      CU(launch_adj_bt_same((int)q, x, o, v, dBT.Kp, dBT.f64, dvv, dt2ss, st));
+      TRY(df_adjoint(R, A, R.Bvv[s], G.dBvv[s], 0, v * v, R.Bov[s], G.dBov[s], (int64_t)x * v, v,
+                     dvv, v * v));
+    }
+    A.drop(dvv);
+  }
+  if (!P.listA1.empty()) {
+    double* djT;
+    TRY(zeros(A, &djT, (int64_t)o * v * ot * ot, st));
+    int2* dl;
+    TRY(upload_pairs(P.listA1, &dl));
+    CU(launch_adj_a1(dl, (int)P.listA1.size(), o, v, ot, vt, dA1.Kp, dA1.f64, dt2st, djT, st));
+    TRY(df_adjoint(R, A, R.Bov[s], G.dBov[s], 0, o * v, R.Boo[t], G.dBoo[t], 0, ot * ot, djT,
+                   o * v));
+    A.drop(djT);
+  }
+  if (!P.listBG.empty()) {
+    double* dgT;
+    TRY(A.get(&dgT, (size_t)v * vt * vt));
+    for (size_t q = 0; q < P.listBG.size(); ++q) {
+      const int x = P.listBG[q];
+      CU(cudaMemsetAsync(dgT, 0, (size_t)v * vt * vt * sizeof(double), st));
+      CU(launch_adj_bg((int)q, x, o, v, ot, vt, dBG.Kp, dBG.f64, dgT, dt2st, st));
+      TRY(df_adjoint(R, A, R.Bvv[t], G.dBvv[t], 0, vt * vt, R.Bov[s], G.dBov[s], (int64_t)x * v, v,
+                     dgT, vt * vt));
+    }
+    A.drop(dgT);
+  }
+  if (!P.listBF.empty()) {
+    double* dfT;
+    TRY(A.get(&dfT, (size_t)vt * v * v));
+    for (size_t q = 0; q < P.listBF.size(); ++q) {
+      const int K = P.listBF[q];
+      CU(cudaMemsetAsync(dfT, 0, (size_t)vt * v * v * sizeof(double), st));
+      CU(launch_adj_bf((int)q, K, o, v, ot, vt, dBF.Kp, dBF.f64, dfT, dt2st, st));
+      TRY(df_adjoint(R, A, R.Bvv[s], G.dBvv[s], 0, v * v, R.Bov[t], G.dBov[t], (int64_t)K * vt, vt,
+                     dfT, v * v));
+    }
+    A.drop(dfT);
+  }
+  if (!P.listAT2.empty()) {
+    double* dlT;
+    TRY(zeros(A, &dlT, (int64_t)ot * vt * o * o, st));
+    int2* dl;
+    TRY(upload_pairs(P.listAT2, &dl));
+    CU(launch_adj_at2(dl, (int)P.listAT2.size(), o, v, ot, vt, dAT2.Kp, dAT2.f64, dt2st, dlT, st));
+    TRY(df_adjoint(R, A, R.Boo[s], G.dBoo[s], 0, o * o, R.Bov[t], G.dBov[t], 0, ot * vt, dlT,
+                   o * o));
+    A.drop(dlT);
+  }
+  if (dovov_ts)  // (jb|KC): L = Bov_s rows (j,b), R = Bov_t rows (K,C)
+    TRY(df_adjoint(R, A, R.Bov[s], G.dBov[s], 0, o * v, R.Bov[t], G.dBov[t], 0, ot * vt, dovov_ts,
+                   o * v));
+  if (s == 1 && !P.mixed.trips.empty())
+    CU(launch_adj_transpose_t2ab(dt2st, ot, o, vt, v, G.dt2ab, st));
+  CU(cudaStreamSynchronize(st));
+  return LNO_OT_OK;
+}
+
+int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_grad* g) {
+  TRY(validate(ctx, dom));
+  const int nbas = dom->nbas, naux = dom->naux;
+  const int na = dom->nocc[0], nb = dom->nocc[1];
+  const int va = nbas - na, vb = nbas - nb;
+  const int64_t nB = (int64_t)naux * nbas * nbas;
+  const int64_t n1[2] = {(int64_t)na * va, (int64_t)nb * vb};
+  const int64_t naa = (int64_t)na * na * va * va, nbb = (int64_t)nb * nb * vb * vb,
+                nab = (int64_t)na * nb * va * vb;
+  for (int s = 0; s < 2; ++s) {
+    TRY(check_ptr(ctx, g->dB[s], false));
+    TRY(check_ptr(ctx, g->deps[s], false));
+    TRY(check_ptr(ctx, g->dt1[s], false));
+  }
+  TRY(check_ptr(ctx, g->dt2aa, false));
+  TRY(check_ptr(ctx, g->dt2bb, false));
+  TRY(check_ptr(ctx, g->dt2ab, false));
+  CU(cudaSetDevice(ctx->device));
+  ctx->stats = lno_ot_stats{};
+  ctx->ev_used = 0;
+  Run R(ctx, dom);
+  R.f64 = true;
+  R.S = 0;
+  CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+  CaseSel cs[4];
+  for (int c = 0; c < 4; ++c) TRY(select_case(dom, c, cs[c]));
+  TRY(R.stage());
+  Arena GA(R.st, 0);
+  GradAcc G{};
+  for (int s = 0; s < 2; ++s) {
+    TRY(zero_operand_like(GA, R.Boo[s], G.dBoo[s], R.st));
+    TRY(zero_operand_like(GA, R.Bov[s], G.dBov[s], R.st));
+    TRY(zero_operand_like(GA, R.Bvv[s], G.dBvv[s], R.st));
+    TRY(zeros(GA, &G.dovov_ss[s], n1[s] * n1[s], R.st));
+    TRY(zeros(GA, &G.dt1[s], n1[s], R.st));
+    TRY(zeros(GA, &G.deps[s], nbas, R.st));
+  }
+  TRY(zeros(GA, &G.dt2aa, naa, R.st));
+  TRY(zeros(GA, &G.dt2bb, nbb, R.st));
+  TRY(zeros(GA, &G.dt2ab, nab, R.st));
+  double* e_dummy[4];
+  for (int c = 0; c < 4; ++c)
+    TRY(GA.get(&e_dummy[c], std::max<size_t>(cs[c].trips.size(), 1)));
+  for (int s = 0; s < 2; ++s) {
+    SpinPass P(R, s, s == 0 ? cs[0] : cs[3], s == 0 ? cs[1] : cs[2], e_dummy[s == 0 ? 0 : 3],
+               e_dummy[s == 0 ? 1 : 2]);
+    if (P.same.trips.empty() && P.mixed.trips.empty()) continue;
+    P.plan();
+    TRY(P.prepare_inputs());
+    if (!P.mixed.trips.empty()) {
+      const int64_t nr = (int64_t)P.o * P.v, nc = (int64_t)P.ot * P.vt;
+      TRY(P.own.get(&P.ovov_ts, (size_t)std::max<int64_t>(nr * nc, 1)));
+      TRY(R.df(R.Bov[s], 0, (int)nr, R.Bov[1 - s], 0, (int)nc, P.ovov_ts, (int)nr));
+    }
+    TRY(P.build());
+    TRY(backward_spin(P, G, gE));
+  }
+  // (ia|jb) of each spin: L = R = Bov_s
+  for (int s = 0; s < 2; ++s)
+    TRY(df_adjoint(R, GA, R.Bov[s], G.dBov[s], 0, (int)n1[s], R.Bov[s], G.dBov[s], 0, (int)n1[s],
+                   G.dovov_ss[s], (int)n1[s]));
+  // outputs: dB (symmetrised), deps, dt1, dt2 (antisymmetrised same-spin)
+  for (int s = 0; s < 2; ++s) {
+    const int o = dom->nocc[s], v = nbas - o;
+    if (g->dB[s]) {
+      double* raw;
+      TRY(zeros(GA, &raw, nB, R.st));
+      CU(launch_adj_transpose_block(G.dBoo[s].f64, naux, nbas, 0, o, 0, o, G.dBoo[s].Kp, raw, R.st));
+      CU(launch_adj_transpose_block(G.dBov[s].f64, naux, nbas, 0, o, o, v, G.dBov[s].Kp, raw, R.st));
+      CU(launch_adj_transpose_block(G.dBvv[s].f64, naux, nbas, o, v, o, v, G.dBvv[s].Kp, raw, R.st));
+      CU(launch_sym_project(raw, naux, nbas, 1.0, g->dB[s], R.st));
+    }
+    if (g->deps[s]) CU(launch_scale_copy(G.deps[s], nbas, 1.0, g->deps[s], R.st));
+    if (g->dt1[s]) CU(launch_scale_copy(G.dt1[s], n1[s], 1.0, g->dt1[s], R.st));
+  }
+  if (g->dt2aa) CU(launch_antisym_project(G.dt2aa, na, va, 1.0, g->dt2aa, R.st));
+  if (g->dt2bb) CU(launch_antisym_project(G.dt2bb, nb, vb, 1.0, g->dt2bb, R.st));
+  if (g->dt2ab) CU(launch_scale_copy(G.dt2ab, nab, 1.0, g->dt2ab, R.st));
+  CU(cudaStreamSynchronize(R.st));
+  int flag = 0;
+  CU(cudaMemcpy(&flag, ctx->d_flag, sizeof flag, cudaMemcpyDeviceToHost));
+  return flag ? LNO_OT_ETIMEOUT : LNO_OT_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1028,15 +1448,9 @@ int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
     const char* ev = getenv("LNO_OT_CLUSTER");
     c->cluster = !(ev && ev[0] == '0');
   }
-  if (opt->stream) {
-    c->stream = static_cast<cudaStream_t>(opt->stream);
-  } else {
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete c;
-      return LNO_OT_ECUDA;
-    }
-    c->own_stream = true;
-  }
+  // NULL = the legacy default stream (ordered with every blocking stream)
+  c->stream = static_cast<cudaStream_t>(opt->stream);
+  c->own_stream = false;
   // keep freed stream-ordered memory in the pool between calls
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
@@ -1101,9 +1515,9 @@ int lno_ot_energy_batched(lno_ot_ctx* ctx, int ndom, const lno_ot_domain* doms,
 }
 
 int lno_ot_backward(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_grad* g) {
-  (void)gE;
   if (!ctx || !dom || !g) return LNO_OT_EINVAL;
-  return LNO_OT_EUNSUPPORTED;
+  if (!std::isfinite(gE)) return LNO_OT_EINVAL;
+  return backward_impl(ctx, dom, gE, g);
 }
 
 int lno_ot_last_stats(const lno_ot_ctx* ctx, lno_ot_stats* st) {

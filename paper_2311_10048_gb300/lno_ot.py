@@ -156,6 +156,10 @@ class Context:
     def __init__(self, device=0, precision="fp64", stream=None, workspace_bytes=0):
         self.lib = load_library()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if stream is None:  # order the library's work after torch's pending work
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream(device).cuda_stream or None
         opt = Options(device, prec, None if stream is None else C.c_void_p(stream), workspace_bytes,
                       None)
         h = C.c_void_p()
@@ -206,10 +210,10 @@ class Context:
         out = [dict(zip(CASES + ("total",), list(r.e)), status=r.status) for r in res]
         return rc, out
 
-    def backward(self, dom, gE, grads):
+    def backward(self, dom, gE, grads, trip_sel=None):
         """grads: dict with optional device tensors dB, deps (lists), dt1 (list),
         dt2aa, dt2bb, dt2ab; overwritten with gE * dE/d(input)."""
-        d, keep = make_domain_struct(dom)
+        d, keep = make_domain_struct(dom, trip_sel=trip_sel)
         g = Grad()
         for s in (0, 1):
             for key in ("dB", "deps", "dt1"):
@@ -241,3 +245,55 @@ def to_device(dom, device="cuda"):
                 B=[t(dom["B"][0]), t(dom["B"][1])], eps=[t(dom["eps"][0]), t(dom["eps"][1])],
                 t1=[t(dom["t1"][0]), t(dom["t1"][1])], t2aa=t(dom["t2aa"]),
                 t2bb=t(dom["t2bb"]), t2ab=t(dom["t2ab"]))
+
+
+def _triples_autograd():
+    import torch
+
+    class LnoTriples(torch.autograd.Function):
+        """E(T) of one domain as a differentiable scalar.
+
+        Forward calls lno_ot_energy (the context's precision); backward calls
+        lno_ot_backward (float64 adjoint, W recomputed per triplet).  Inputs
+        are the device tensors of the domain; gradients of B and of the
+        same-spin T2 blocks are projected onto their symmetry.
+        """
+
+        @staticmethod
+        def forward(fctx, Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab, meta):
+            handle, nocc, naux, trip_sel = meta
+            dom = dict(nbas=Ba.shape[1], naux=naux, nocc=nocc, B=[Ba, Bb], eps=[ea, eb],
+                       t1=[t1a, t1b], t2aa=t2aa, t2bb=t2bb, t2ab=t2ab)
+            out = handle.energy(dom, trip_sel=trip_sel)
+            fctx.save_for_backward(Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab)
+            fctx.meta = meta
+            return torch.tensor(out["total"], dtype=torch.float64, device=Ba.device)
+
+        @staticmethod
+        def backward(fctx, gE):
+            Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab = fctx.saved_tensors
+            handle, nocc, naux, trip_sel = fctx.meta
+            dom = dict(nbas=Ba.shape[1], naux=naux, nocc=nocc, B=[Ba, Bb], eps=[ea, eb],
+                       t1=[t1a, t1b], t2aa=t2aa, t2bb=t2bb, t2ab=t2ab)
+            need = fctx.needs_input_grad
+            z = lambda x, k: torch.empty_like(x) if need[k] else None
+            g = dict(dB=[z(Ba, 0), z(Bb, 1)], deps=[z(ea, 2), z(eb, 3)], dt1=[z(t1a, 4), z(t1b, 5)],
+                     dt2aa=z(t2aa, 6), dt2bb=z(t2bb, 7), dt2ab=z(t2ab, 8))
+            handle.backward(dom, float(gE), g, trip_sel=trip_sel)
+            return (g["dB"][0], g["dB"][1], g["deps"][0], g["deps"][1], g["dt1"][0], g["dt1"][1],
+                    g["dt2aa"], g["dt2bb"], g["dt2ab"], None)
+
+    return LnoTriples
+
+
+_LNO_FN = None
+
+
+def triples_energy(ctx, dom, trip_sel=None):
+    """Differentiable E(T) (torch scalar) of a domain dict of device tensors."""
+    global _LNO_FN
+    if _LNO_FN is None:
+        _LNO_FN = _triples_autograd()
+    return _LNO_FN.apply(dom["B"][0], dom["B"][1], dom["eps"][0], dom["eps"][1], dom["t1"][0],
+                         dom["t1"][1], dom["t2aa"], dom["t2bb"], dom["t2ab"],
+                         (ctx, tuple(dom["nocc"]), int(dom["naux"]), trip_sel))
