@@ -119,19 +119,31 @@ def make_domain(nbas, nocc, naux, L, seed, t1_sd=1e-3, closed_shell=False):
 
 
 def mp2_like_t2(Ba, ea, na, Bb, eb, nb):
-    """MP2-like doubles from B and eps (input recipe, see module docstring)."""
+    """MP2-like doubles from B and eps (input recipe, see module docstring).
+
+    The element-wise part runs one first occupied index at a time, so the
+    peak host memory is the (ia|jb) block plus the outputs.
+    """
     out = {}
     for key, (Bp, ep, op) in (("t2aa", (Ba, ea, na)), ("t2bb", (Bb, eb, nb))):
         g = _ovov(Bp, op, Bp, op)                       # [i][a][j][b]
-        num = g.transpose(0, 2, 1, 3) - g.transpose(0, 2, 3, 1)
         eo, ev = ep[:op], ep[op:]
-        d2 = (eo[:, None, None, None] + eo[None, :, None, None]
-              - ev[None, None, :, None] - ev[None, None, None, :])
-        out[key] = np.ascontiguousarray(num / d2)
-    g = _ovov(Ba, na, Bb, nb).transpose(0, 2, 1, 3)   # [i][J][a][B]
-    d2 = (ea[:na][:, None, None, None] + eb[:nb][None, :, None, None]
-          - ea[na:][None, None, :, None] - eb[nb:][None, None, None, :])
-    out["t2ab"] = np.ascontiguousarray(g / d2)
+        nv = ev.size
+        t2 = np.empty((op, op, nv, nv))
+        for i in range(op):
+            gi = g[i]                                    # [a][j][b]
+            num = gi.transpose(1, 0, 2) - gi.transpose(1, 2, 0)   # [j][a][b]
+            d2 = (eo[i] + eo)[:, None, None] - ev[None, :, None] - ev[None, None, :]
+            t2[i] = num / d2
+        out[key] = t2
+        del g
+    g = _ovov(Ba, na, Bb, nb)                            # [i][a][J][B]
+    eoa, eva, eob, evb = ea[:na], ea[na:], eb[:nb], eb[nb:]
+    t2 = np.empty((na, nb, eva.size, evb.size))
+    for i in range(na):
+        d2 = (eoa[i] + eob)[:, None, None] - eva[None, :, None] - evb[None, None, :]
+        t2[i] = g[i].transpose(1, 0, 2) / d2
+    out["t2ab"] = t2
     return out
 
 

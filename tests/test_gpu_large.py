@@ -83,10 +83,16 @@ def test_c2_sampled_parity_both_paths(lib):
     rng = np.random.default_rng(2024)
     sel = [np.sort(rng.choice(n_trip(c, na, nb), size=2, replace=False)).astype(np.int64)
            for c in CASES]
-    ev = Evaluator(d)
-    ref = [[float(ev.triplet_energy(c, triplets(c, na, nb)[int(q)])) for q in sel[ci]]
-           for ci, c in enumerate(CASES)]
-    del ev
+    # share the numpy buffers with the oracle (no second copy of ~75 GB)
+    dt = dict(nbas=d["nbas"], naux=d["naux"], nocc=d["nocc"],
+              B=[torch.from_numpy(x) for x in d["B"]], eps=[torch.from_numpy(x) for x in d["eps"]],
+              t1=[torch.from_numpy(x) for x in d["t1"]],
+              **{k: torch.from_numpy(d[k]) for k in ("t2aa", "t2bb", "t2ab")})
+    ev = Evaluator(dt)
+    with torch.no_grad():
+        ref = [[float(ev.triplet_energy(c, triplets(c, na, nb)[int(q)])) for q in sel[ci]]
+               for ci, c in enumerate(CASES)]
+    del ev, dt
     dd = lno_ot.to_device(d)
     res = {}
     for prec, tol in (("fp64", 1e-8), ("bf16x6", 1e-7)):
