@@ -78,7 +78,13 @@ typedef struct {
   void* stream;           /* cudaStream_t to order all work on; NULL = the
                              legacy default stream */
   size_t workspace_bytes; /* upper bound on device workspace; 0 = no bound */
-  const char* tune_cache; /* reserved, may be NULL */
+  const char* tune_cache; /* NULL, or a tuning table written by the autotuner
+                             (paper_2311_10048_gb300/tune.py): text lines
+                             "vmax cluster group_cap" giving, per bucket of
+                             virtual-space size, the contraction variant
+                             (1 = 2-CTA multicast clusters) and the cap on
+                             triplets per contraction launch.  Unreadable
+                             file: lno_ot_init returns LNO_OT_EINVAL. */
 } lno_ot_options;
 
 /* One domain.  Orbitals of each spin are ordered occupied first (ascending

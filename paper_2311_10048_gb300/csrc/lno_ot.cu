@@ -130,6 +130,17 @@ struct lno_ot_ctx {
   size_t ws_limit = 0;
   int nsm = 152;
   bool cluster = true;                 // W contractions in 2-CTA multicast clusters
+  // tuning table: per virtual-space size bucket (rows of the contraction,
+  // ascending vmax) the contraction variant and the triplet-group cap
+  struct TuneRow {
+    int vmax, cluster, group_cap;
+  };
+  std::vector<TuneRow> tune;
+  const TuneRow* tune_for(int v) const {
+    for (const TuneRow& r : tune)
+      if (v <= r.vmax) return &r;
+    return tune.empty() ? nullptr : &tune.back();
+  }
   int* d_flag = nullptr;               // device error flag (bounded waits)
   unsigned long long* d_amax = nullptr;
   double* d_sums = nullptr;            // [8]
@@ -456,6 +467,8 @@ struct SpinPass {
   std::vector<int> slotAT, slotBT, slotA1, slotBG, slotBF, slotAT2;  // -1 = unused
   std::vector<int2> listAT, listA1, listAT2;
   std::vector<int> listBT, listBG, listBF;
+  bool use_cluster = true;   // contraction variant of the current case
+  int group_cap = 64;        // triplets per group (upper bound)
   double* t2st = nullptr;    // [os][ot][vs][vt]
   const double* t2ss = nullptr;
   double* ovov_ts = nullptr; // (jb|KC) as [ot][vt][os][vs]
@@ -668,7 +681,7 @@ struct SpinPass {
       const double scale = R.sigT * R.sigI * std::ldexp(1.0, -14);
       int* fl = R.ctx->d_flag;
       const int nsm = R.ctx->nsm;
-      if (R.ctx->cluster) {
+      if (use_cluster) {
         if (R.S == 2)
           CU(launch_tc_gemm_mc<2, 256, float>(mA64, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr,
                                               nsm, R.st));
@@ -714,7 +727,14 @@ struct SpinPass {
     const int P2 = (int)round_up(std::max(M2, 1), 16);
     const int64_t per_trip = (N1 * P1 + N2 * P2) * (int64_t)esz;
     const int64_t budget = (int64_t)6 << 30;
-    int G = (int)std::max<int64_t>(1, std::min<int64_t>(64, budget / std::max<int64_t>(per_trip, 1)));
+    use_cluster = R.ctx->cluster;
+    group_cap = 64;
+    if (const auto* row = R.ctx->tune_for(v)) {
+      use_cluster = row->cluster != 0;
+      group_cap = std::max(1, row->group_cap);
+    }
+    int G = (int)std::max<int64_t>(
+        1, std::min<int64_t>(group_cap, budget / std::max<int64_t>(per_trip, 1)));
     G = std::min(G, ntrip);
     char *X = nullptr, *Z = nullptr;
     TRY(A.get(&X, (size_t)(G * N1 * P1 * esz) + 64));
@@ -1447,6 +1467,23 @@ int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
   {  // kernel variant of the W contractions (tuning knob; default: clusters)
     const char* ev = getenv("LNO_OT_CLUSTER");
     c->cluster = !(ev && ev[0] == '0');
+  }
+  if (opt->tune_cache && opt->tune_cache[0]) {  // "vmax cluster group_cap" per line
+    FILE* f = fopen(opt->tune_cache, "r");
+    if (!f) {
+      lno_ot_destroy(c);
+      return LNO_OT_EINVAL;
+    }
+    char line[256];
+    while (fgets(line, sizeof line, f)) {
+      if (line[0] == '#') continue;
+      lno_ot_ctx::TuneRow r;
+      if (sscanf(line, "%d %d %d", &r.vmax, &r.cluster, &r.group_cap) == 3 && r.vmax > 0)
+        c->tune.push_back(r);
+    }
+    fclose(f);
+    std::sort(c->tune.begin(), c->tune.end(),
+              [](const lno_ot_ctx::TuneRow& a, const lno_ot_ctx::TuneRow& b) { return a.vmax < b.vmax; });
   }
   // NULL = the legacy default stream (ordered with every blocking stream)
   c->stream = static_cast<cudaStream_t>(opt->stream);

@@ -153,15 +153,17 @@ def make_domain_struct(dom, e_trip=None, trip_sel=None):
 class Context:
     """An lno_ot context (device, precision, stream)."""
 
-    def __init__(self, device=0, precision="fp64", stream=None, workspace_bytes=0):
+    def __init__(self, device=0, precision="fp64", stream=None, workspace_bytes=0,
+                 tune_cache=None):
         self.lib = load_library()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if stream is None:  # order the library's work after torch's pending work
             import torch
             if torch.cuda.is_available():
                 stream = torch.cuda.current_stream(device).cuda_stream or None
+        self._tune = None if tune_cache is None else str(tune_cache).encode()
         opt = Options(device, prec, None if stream is None else C.c_void_p(stream), workspace_bytes,
-                      None)
+                      self._tune)
         h = C.c_void_p()
         rc = self.lib.lno_ot_init(C.byref(h), C.byref(opt))
         if rc != OK:
