@@ -297,6 +297,51 @@ def run_c3(args):
     return 0
 
 
+def run_backward(args):
+    """Adjoint timing: lno_ot_backward (float64, W recomputed per triplet) on a
+    seeded triplet sample of the domain, against its forward on the same sample."""
+    import torch
+    from paper_2311_10048_gb300 import lno_ot
+    cfg = dict(CONFIGS[args.config])
+    dom = make_domain(**cfg)
+    nbas, nocc = dom["nbas"], dom["nocc"]
+    sel = sample_triplets(nocc, args.bwd_sample, seed=13)
+    dev = torch.device("cuda", 0)
+    dd = lno_ot.to_device(dom, dev)
+    ctx = lno_ot.Context(0, "fp64")
+    g = dict(dB=[torch.empty_like(dd["B"][0]), torch.empty_like(dd["B"][1])],
+             deps=[torch.empty_like(dd["eps"][0]), torch.empty_like(dd["eps"][1])],
+             dt1=[torch.empty_like(dd["t1"][0]), torch.empty_like(dd["t1"][1])],
+             dt2aa=torch.empty_like(dd["t2aa"]), dt2bb=torch.empty_like(dd["t2bb"]),
+             dt2ab=torch.empty_like(dd["t2ab"]))
+    ctx.backward(dd, 1.0, g, trip_sel=sel)        # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.backward(dd, 1.0, g, trip_sel=sel)
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx.energy(dd, trip_sel=sel)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    fst = ctx.stats()
+    ctx.close()
+    ntr = sum(len(x) for x in sel)
+    flops = sum(alg_flops_triplet(c, nocc, nbas) * len(sel[ci]) for ci, c in enumerate(CASES))
+    line = {"metric": "E(T) adjoint (dE/dB, deps, dT1, dT2) wall time on a triplet sample",
+            "value": t_bwd, "unit": "s", "higher_is_better": False, "dtype": "f64",
+            "data": "synthetic", "steps": 1, "warmup": 1,
+            "config": {"workload": workload_name(args.config) + " (adjoint)", **cfg_public(cfg),
+                       "sample": f"{ntr} seeded triplets ({', '.join(f'{c}:{len(sel[i])}' for i, c in enumerate(CASES))})"},
+            "forward_same_sample_s": t_fwd,
+            "backward_over_forward": t_bwd / t_fwd,
+            "sample_algorithmic_flops": flops,
+            "forward_breakdown_ms": {k: fst[k] for k in ("ms_stage", "ms_contract", "ms_energy")},
+            "w_recomputed_per_triplet": True}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,6 +350,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c1", choices=sorted(CONFIGS) + ["custom", "c3"])
     ap.add_argument("--c3-sample", type=int, default=8, help="domains of the c3 batch")
+    ap.add_argument("--backward", action="store_true", help="time the adjoint on a sample")
+    ap.add_argument("--bwd-sample", type=int, default=1, help="adjoint triplets per case")
     ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x3"])
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle triplets per case")
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
@@ -323,6 +370,8 @@ def main():
         return run_reference(args)
     if args.config == "c3":
         return run_c3(args)
+    if args.backward:
+        return run_backward(args)
 
     import torch
     import torch.distributed as dist
