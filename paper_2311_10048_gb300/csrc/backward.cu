@@ -507,6 +507,60 @@ __global__ void antisym_project(const double* __restrict__ G, int o, int v, doub
   }
 }
 
+// In place: G[Q][p][q], G[Q][q][p] <- (G[Q][p][q] + G[Q][q][p]) / 2
+__global__ void sym_inplace(double* __restrict__ G, int naux, int n) {
+  const int64_t np = (int64_t)n * (n - 1) / 2;
+  const int64_t total = (int64_t)naux * np;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t Q = idx / np, pr = idx % np;
+    int q = (int)((1.0 + sqrt(1.0 + 8.0 * (double)pr)) * 0.5);
+    while ((int64_t)q * (q - 1) / 2 > pr) --q;
+    while ((int64_t)(q + 1) * q / 2 <= pr) ++q;
+    const int p = (int)(pr - (int64_t)q * (q - 1) / 2);
+    double* x = G + (Q * n + p) * n + q;
+    double* y = G + (Q * n + q) * n + p;
+    const double m = 0.5 * (*x + *y);
+    *x = m;
+    *y = m;
+  }
+}
+
+// In place over one index pair of [o][o][v][v]: first (i,j), then (a,b):
+// X <- (X - X^T)/2 (diagonal -> 0).  Both passes give (G-G_ji-G_ba+G_jiba)/4.
+__global__ void antisym_inplace_occ(double* __restrict__ G, int o, int v) {
+  const int64_t vv = (int64_t)v * v;
+  const int64_t total = (int64_t)o * o * vv;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ab = idx % vv, ij = idx / vv;
+    const int i = (int)(ij / o), j = (int)(ij % o);
+    if (i > j) continue;
+    double* x = G + ((int64_t)i * o + j) * vv + ab;
+    if (i == j) { *x = 0.0; continue; }
+    double* y = G + ((int64_t)j * o + i) * vv + ab;
+    const double d = 0.5 * (*x - *y);
+    *x = d;
+    *y = -d;
+  }
+}
+__global__ void antisym_inplace_vir(double* __restrict__ G, int o, int v) {
+  const int64_t vv = (int64_t)v * v;
+  const int64_t total = (int64_t)o * o * vv;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ij = idx / vv, ab = idx % vv;
+    const int a = (int)(ab / v), b = (int)(ab % v);
+    if (a > b) continue;
+    double* x = G + ij * vv + (int64_t)a * v + b;
+    if (a == b) { *x = 0.0; continue; }
+    double* y = G + ij * vv + (int64_t)b * v + a;
+    const double d = 0.5 * (*x - *y);
+    *x = d;
+    *y = -d;
+  }
+}
+
 // dt2ab[k][I][c][A] += dt2ba[I][k][A][c]
 __global__ void adj_transpose_t2ab(const double* __restrict__ dt2ba, int na, int nb, int va, int vb,
                                    double* __restrict__ dt2ab) {
@@ -624,6 +678,19 @@ cudaError_t launch_antisym_project(const double* G, int o, int v, double scale, 
   int64_t m = (int64_t)o * o * v * v;
   if (m == 0) return cudaSuccess;
   antisym_project<<<grid_for(m), 256, 0, st>>>(G, o, v, scale, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_sym_inplace(double* G, int naux, int n, cudaStream_t st) {
+  int64_t m = (int64_t)naux * n * (n - 1) / 2;
+  if (m == 0) return cudaSuccess;
+  sym_inplace<<<grid_for(m), 256, 0, st>>>(G, naux, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_antisym_inplace(double* G, int o, int v, cudaStream_t st) {
+  int64_t m = (int64_t)o * o * v * v;
+  if (m == 0) return cudaSuccess;
+  antisym_inplace_occ<<<grid_for(m), 256, 0, st>>>(G, o, v);
+  antisym_inplace_vir<<<grid_for(m), 256, 0, st>>>(G, o, v);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_transpose_t2ab(const double* dt2ba, int na, int nb, int va, int vb,

@@ -368,18 +368,21 @@ __device__ __forceinline__ float div_nr(float num, float D) {
 }
 
 // Energy of float32 X with register prefetch of the next cube tile.
-// Shared layout per tile (thread (b,c) loops over a):
-//   T1[b][c][a] rows of 20 floats (16-byte aligned: read as float4)
-//   T2[a][c][b], T3[a][b][c] rows of 17 floats (conflict-free scalar reads)
-//   ad[a]   = {t1 of the triplet's occupied on a (up to 3), eps_a hi}, ael[a] = eps_a lo
-//   kac[a][c], kab[a][b]: float4 of the V-table planes on (A,C) and (A,B)
+// Work split inside a 16^3 tile: thread (c, b-pair, a-half) computes the 16
+// elements a in [8h, 8h+8), b in {2p, 2p+1}, c; values that depend on a only
+// (T1 amplitudes, orbital energy, V planes on (a,c)) are loaded once for both
+// b.  Shared layout (pitches chosen for conflict-free vector reads):
+//   T1[b][c][a] pitch 20 (float4 along a)   X[a,(bc)] / Y[a,(bC)]
+//   T2[a][c][b] pitch 18 (float2 along b)   X[b,(ac)] / Y[b,(aC)]
+//   T3[a][b][c] pitch 24                    X[c,(ab)] / Z'[C,(ab)]
 template <bool MIXED>
 __global__ void __launch_bounds__(256, 2)
 energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ Z,
            const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt) {
-  constexpr int P1 = 20;
+  constexpr int P1 = 20, P2 = 18, P3 = 24;
   __shared__ __align__(16) float T1[TB * TB * P1];
-  __shared__ float T2[TB * TB * TP], T3[TB * TB * TP];
+  __shared__ __align__(16) float T2[TB * TB * P2];
+  __shared__ __align__(16) float T3[TB * TB * P3];
   __shared__ __align__(16) float4 kac[TB][TB];
   __shared__ __align__(16) float4 kab[TB][TB];
   __shared__ float kbc[3][TB][TP];
@@ -395,7 +398,11 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   const float* Zg = MIXED ? Z + (int64_t)g * a.z_stride : nullptr;
   const float* Vg = VT + (int64_t)g * vt_stride;
   const int tid = threadIdx.x;
-  const int r1 = tid / TB, r2 = tid % TB;
+  const int r1 = tid / TB, r2 = tid % TB;           // row owned in the fetch phase
+  const int lane = tid & 31, wid = tid >> 5;
+  const int cl = lane & 15;                          // compute phase: c
+  const int bl0 = 2 * (((wid & 3) << 1) | (lane >> 4));   // first of the b pair
+  const int al0 = 8 * (wid >> 2);                    // a half
   const int nvs = a.nvs, nvt = a.nvt;
   const TwoF eocc = split_df(MIXED ? a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_t[tr.k]
                                    : a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_s[tr.k]);
@@ -495,13 +502,16 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
     // ---- registers -> shared ----
     {
       float4* d1 = reinterpret_cast<float4*>(T1 + (r1 * TB + r2) * P1);
-      float* d2 = T2 + (r1 * TB + r2) * TP;
-      float* d3 = T3 + (r1 * TB + r2) * TP;
+      float2* d2 = reinterpret_cast<float2*>(T2 + (r1 * TB + r2) * P2);
+      float4* d3 = reinterpret_cast<float4*>(T3 + (r1 * TB + r2) * P3);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (ok1) d1[u] = xr[0][u];
-        if (ok2) { d2[4 * u] = xr[1][u].x; d2[4 * u + 1] = xr[1][u].y; d2[4 * u + 2] = xr[1][u].z; d2[4 * u + 3] = xr[1][u].w; }
-        if (ok3) { d3[4 * u] = xr[2][u].x; d3[4 * u + 1] = xr[2][u].y; d3[4 * u + 2] = xr[2][u].z; d3[4 * u + 3] = xr[2][u].w; }
+        if (ok2) {
+          d2[2 * u] = make_float2(xr[1][u].x, xr[1][u].y);
+          d2[2 * u + 1] = make_float2(xr[1][u].z, xr[1][u].w);
+        }
+        if (ok3) d3[u] = xr[2][u];
       }
       if (!MIXED) {
         kbc[0][r1][r2] = vr[0]; kbc[1][r1][r2] = vr[1]; kbc[2][r1][r2] = vr[2];
@@ -527,46 +537,64 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
     }
     __syncthreads();
     if (q + (int)gridDim.x < a.nblocks) fetch(q + gridDim.x);  // next tile in flight
-    // ---- elements: thread (b = r1, c = r2), loop over a ----
+    // ---- elements: (a in half, b pair, c) ----------------------------------
     {
-      const int bl = r1, cl = r2;
-      const int b = b0 + bl, c = c0 + cl;
-      const bool rowok = MIXED ? (b < nvs && c < nvt) : (b < c && c < nvs);
-      if (rowok) {
-        const TwoF dbc = df_sub(df_sub(eocc, TwoF{ebh[0][bl], ebl[0][bl]}), TwoF{ebh[1][cl], ebl[1][cl]});
-        const int na = min(b, a0 + TB) - a0;
-        const float4* x1v = reinterpret_cast<const float4*>(T1 + (bl * TB + cl) * P1);
-        const float* x2p = T2 + cl * TP + bl;
-        const float* x3p = T3 + bl * TP + cl;
-        float part = 0.f;
-        const float k0 = kbc[0][bl][cl], k1 = kbc[1][bl][cl], k2 = kbc[2][bl][cl];
-        const float tb0 = tb_s[0][bl], tb1 = tb_s[1][bl], tb2 = tb_s[2][bl];
-        const float tc0 = tc_s[0][cl], tc1 = tc_s[1][cl], tc2 = tc_s[2][cl];
-        for (int a4 = 0; a4 < na; a4 += 4) {
-          const float4 x1q = x1v[a4 >> 2];
-          const float x1a[4] = {x1q.x, x1q.y, x1q.z, x1q.w};
+      const int c = c0 + cl;
+      float part = 0.f;
+      bool rowok[2];
+      TwoF dbc[2];
+      float k0[2], k1[2], k2[2], tb0[2], tb1[2], tb2[2];
+#pragma unroll
+      for (int sb = 0; sb < 2; ++sb) {
+        const int bl = bl0 + sb, b = b0 + bl;
+        rowok[sb] = MIXED ? (b < nvs && c < nvt) : (b < c && c < nvs);
+        dbc[sb] = df_sub(df_sub(eocc, TwoF{ebh[0][bl], ebl[0][bl]}), TwoF{ebh[1][cl], ebl[1][cl]});
+        k0[sb] = kbc[0][bl][cl]; k1[sb] = kbc[1][bl][cl]; k2[sb] = kbc[2][bl][cl];
+        tb0[sb] = tb_s[0][bl]; tb1[sb] = tb_s[1][bl]; tb2[sb] = tb_s[2][bl];
+      }
+      const float tc0 = tc_s[0][cl], tc1 = tc_s[1][cl], tc2 = tc_s[2][cl];
+      // last a (exclusive) any element of this thread can use: a < b <= b0+bl0+1
+      const int aend = min(al0 + 8, b0 + bl0 + 1 - a0);
+      if ((rowok[0] || rowok[1]) && aend > al0) {
+        const float* x1r0 = T1 + ((bl0 + 0) * TB + cl) * P1;
+        const float* x1r1 = T1 + ((bl0 + 1) * TB + cl) * P1;
+        for (int a4 = al0; a4 < aend; a4 += 4) {
+          const float4 q0 = *reinterpret_cast<const float4*>(x1r0 + a4);
+          const float4 q1 = *reinterpret_cast<const float4*>(x1r1 + a4);
+          const float x1a[2][4] = {{q0.x, q0.y, q0.z, q0.w}, {q1.x, q1.y, q1.z, q1.w}};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int al = a4 + u;
-            if (al < na) {
-              const float w = x1a[u] - x2p[al * (TB * TP)] + x3p[al * (TB * TP)];
+            if (al < aend) {
               const float4 da = ad[al];
+              const float del = ael[al];
+              const float2 x2 = *reinterpret_cast<const float2*>(T2 + (al * TB + cl) * P2 + bl0);
               const float4 vac = kac[al][cl];
-              const float4 vab = kab[al][bl];
-              float v;
-              if (!MIXED) {
-                const float ya = da.x * k0 + da.y * k1 + da.z * k2;
-                const float yb = tb0 * vac.x + tb1 * vac.y + tb2 * vac.z;
-                const float yc = tc0 * vab.x + tc1 * vab.y + tc2 * vab.z;
-                v = ya - yb + yc;
-              } else {
-                v = da.x * k0 - da.y * k1 - tb0 * vac.x + tb1 * vac.y + tc0 * vab.x;
+              const float x2a[2] = {x2.x, x2.y};
+#pragma unroll
+              for (int sb = 0; sb < 2; ++sb) {
+                const int bl = bl0 + sb;
+                if (rowok[sb] && a0 + al < b0 + bl) {
+                  const float x3 = T3[(al * TB + bl) * P3 + cl];
+                  const float4 vab = kab[al][bl];
+                  const float w = x1a[sb][u] - x2a[sb] + x3;
+                  float v;
+                  if (!MIXED) {
+                    const float ya = da.x * k0[sb] + da.y * k1[sb] + da.z * k2[sb];
+                    const float yb = tb0[sb] * vac.x + tb1[sb] * vac.y + tb2[sb] * vac.z;
+                    const float yc = tc0 * vab.x + tc1 * vab.y + tc2 * vab.z;
+                    v = ya - yb + yc;
+                  } else {
+                    v = da.x * k0[sb] - da.y * k1[sb] - tb0[sb] * vac.x + tb1[sb] * vac.y +
+                        tc0 * vab.x;
+                  }
+                  const float num = __fmul_rn(w, __fadd_rn(w, v));
+                  float s, e;
+                  two_sum(dbc[sb].hi, -da.w, s, e);
+                  const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc[sb].lo, del)));
+                  part = __fadd_rn(part, div_nr(num, D));
+                }
               }
-              const float num = __fmul_rn(w, __fadd_rn(w, v));
-              float s, e;
-              two_sum(dbc.hi, -da.w, s, e);
-              const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc.lo, ael[al])));
-              part = __fadd_rn(part, div_nr(num, D));
             }
           }
         }
@@ -574,6 +602,8 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
         two_sum(acc.hi, part, s, e);
         acc = {s, __fadd_rn(acc.lo, e)};
       }
+      (void)tc1;
+      (void)tc2;
     }
     __syncthreads();
   }

@@ -109,6 +109,8 @@ cudaError_t launch_sym_project(const double*, int, int, double, double*, cudaStr
 cudaError_t launch_antisym_project(const double*, int, int, double, double*, cudaStream_t);
 cudaError_t launch_adj_transpose_t2ab(const double*, int, int, int, int, double*, cudaStream_t);
 cudaError_t launch_scale_copy(const double*, int64_t, double, double*, cudaStream_t);
+cudaError_t launch_sym_inplace(double*, int, int, cudaStream_t);
+cudaError_t launch_antisym_inplace(double*, int, int, cudaStream_t);
 }  // namespace lno
 
 using namespace lno;
@@ -370,11 +372,15 @@ struct Run {
               StoreSlices<4>{b.op->bf, b.op->slice_stride, 128.0 / sigB, 128.0 / sigB}, st));
       }
     }
-    for (int s = 0; s < 2; ++s) {  // (ia|jb) of spin s
-      const int64_t n = (int64_t)no[s] * nv[s];
-      TRY(arena.get(&ovov_ss[s], (size_t)std::max<int64_t>(n * n, 1)));
-      TRY(df(Bov[s], 0, (int)n, Bov[s], 0, (int)n, ovov_ss[s], (int)n));
-    }
+    return LNO_OT_OK;
+  }
+
+  // (ia|jb) of spin s, in the arena of the spin pass that needs it
+  int ensure_ovov(int s, Arena& ar) {
+    if (ovov_ss[s]) return LNO_OT_OK;
+    const int64_t n = (int64_t)no[s] * nv[s];
+    TRY(ar.get(&ovov_ss[s], (size_t)std::max<int64_t>(n * n, 1)));
+    TRY(df(Bov[s], 0, (int)n, Bov[s], 0, (int)n, ovov_ss[s], (int)n));
     return LNO_OT_OK;
   }
 };
@@ -926,6 +932,7 @@ struct SpinPass {
     if (same.trips.empty() && mixed.trips.empty()) return LNO_OT_OK;
     plan();
     TRY(prepare_inputs());
+    TRY(R.ensure_ovov(s, own));
     if (!mixed.trips.empty()) {
       const int64_t nr = (int64_t)o * v, nc = (int64_t)ot * vt;
       TRY(own.get(&ovov_ts, (size_t)std::max<int64_t>(nr * nc, 1)));
@@ -1010,6 +1017,7 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
     if (t1) cudaEventRecord(t1, R.st);
     TRY(pa.run());
     pa.own.release();
+    R.ovov_ss[0] = nullptr;
     TRY(pb.run());
   }
   // per-case sums
@@ -1389,13 +1397,23 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
     TRY(zero_operand_like(GA, R.Boo[s], G.dBoo[s], R.st));
     TRY(zero_operand_like(GA, R.Bov[s], G.dBov[s], R.st));
     TRY(zero_operand_like(GA, R.Bvv[s], G.dBvv[s], R.st));
-    TRY(zeros(GA, &G.dovov_ss[s], n1[s] * n1[s], R.st));
+    G.dovov_ss[s] = nullptr;
     TRY(zeros(GA, &G.dt1[s], n1[s], R.st));
     TRY(zeros(GA, &G.deps[s], nbas, R.st));
   }
-  TRY(zeros(GA, &G.dt2aa, naa, R.st));
-  TRY(zeros(GA, &G.dt2bb, nbb, R.st));
-  TRY(zeros(GA, &G.dt2ab, nab, R.st));
+  // T2 gradients accumulate in the caller's buffers when given (projected in
+  // place at the end), else in scratch
+  auto acc_buf = [&](double* user, int64_t n, double** out) -> int {
+    if (user) {
+      CU(cudaMemsetAsync(user, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(double), R.st));
+      *out = user;
+      return LNO_OT_OK;
+    }
+    return zeros(GA, out, n, R.st);
+  };
+  TRY(acc_buf(g->dt2aa, naa, &G.dt2aa));
+  TRY(acc_buf(g->dt2bb, nbb, &G.dt2bb));
+  TRY(acc_buf(g->dt2ab, nab, &G.dt2ab));
   double* e_dummy[4];
   for (int c = 0; c < 4; ++c)
     TRY(GA.get(&e_dummy[c], std::max<size_t>(cs[c].trips.size(), 1)));
@@ -1405,6 +1423,9 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
     if (P.same.trips.empty() && P.mixed.trips.empty()) continue;
     P.plan();
     TRY(P.prepare_inputs());
+    TRY(R.ensure_ovov(s, P.own));
+    Arena ov_arena(R.st, 0);
+    TRY(zeros(ov_arena, &G.dovov_ss[s], n1[s] * n1[s], R.st));
     if (!P.mixed.trips.empty()) {
       const int64_t nr = (int64_t)P.o * P.v, nc = (int64_t)P.ot * P.vt;
       TRY(P.own.get(&P.ovov_ts, (size_t)std::max<int64_t>(nr * nc, 1)));
@@ -1412,28 +1433,29 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
     }
     TRY(P.build());
     TRY(backward_spin(P, G, gE));
-  }
-  // (ia|jb) of each spin: L = R = Bov_s
-  for (int s = 0; s < 2; ++s)
+    // (ia|jb) of spin s: L = R = Bov_s
     TRY(df_adjoint(R, GA, R.Bov[s], G.dBov[s], 0, (int)n1[s], R.Bov[s], G.dBov[s], 0, (int)n1[s],
                    G.dovov_ss[s], (int)n1[s]));
+    CU(cudaStreamSynchronize(R.st));
+    R.ovov_ss[s] = nullptr;
+    G.dovov_ss[s] = nullptr;
+  }
   // outputs: dB (symmetrised), deps, dt1, dt2 (antisymmetrised same-spin)
   for (int s = 0; s < 2; ++s) {
     const int o = dom->nocc[s], v = nbas - o;
-    if (g->dB[s]) {
-      double* raw;
-      TRY(zeros(GA, &raw, nB, R.st));
+    if (g->dB[s]) {  // raw gradient into the caller's buffer, symmetrised in place
+      double* raw = g->dB[s];
+      CU(cudaMemsetAsync(raw, 0, (size_t)nB * sizeof(double), R.st));
       CU(launch_adj_transpose_block(G.dBoo[s].f64, naux, nbas, 0, o, 0, o, G.dBoo[s].Kp, raw, R.st));
       CU(launch_adj_transpose_block(G.dBov[s].f64, naux, nbas, 0, o, o, v, G.dBov[s].Kp, raw, R.st));
       CU(launch_adj_transpose_block(G.dBvv[s].f64, naux, nbas, o, v, o, v, G.dBvv[s].Kp, raw, R.st));
-      CU(launch_sym_project(raw, naux, nbas, 1.0, g->dB[s], R.st));
+      CU(launch_sym_inplace(raw, naux, nbas, R.st));
     }
     if (g->deps[s]) CU(launch_scale_copy(G.deps[s], nbas, 1.0, g->deps[s], R.st));
     if (g->dt1[s]) CU(launch_scale_copy(G.dt1[s], n1[s], 1.0, g->dt1[s], R.st));
   }
-  if (g->dt2aa) CU(launch_antisym_project(G.dt2aa, na, va, 1.0, g->dt2aa, R.st));
-  if (g->dt2bb) CU(launch_antisym_project(G.dt2bb, nb, vb, 1.0, g->dt2bb, R.st));
-  if (g->dt2ab) CU(launch_scale_copy(G.dt2ab, nab, 1.0, g->dt2ab, R.st));
+  if (g->dt2aa) CU(launch_antisym_inplace(g->dt2aa, na, va, R.st));
+  if (g->dt2bb) CU(launch_antisym_inplace(g->dt2bb, nb, vb, R.st));
   CU(cudaStreamSynchronize(R.st));
   int flag = 0;
   CU(cudaMemcpy(&flag, ctx->d_flag, sizeof flag, cudaMemcpyDeviceToHost));
