@@ -127,8 +127,8 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
           double v = 0.0;
           if (x < nvs && y < nvs) {
             const int p = occ3[o][0], r = occ3[o][1];
-            v = a.ovov_ss[(((int64_t)p * nvs + x) * nos + r) * nvs + y] -
-                a.ovov_ss[(((int64_t)p * nvs + y) * nos + r) * nvs + x];
+            v = a.ovov_ss[ovss_idx(a, p, x, r, y)] -
+                a.ovov_ss[ovss_idx(a, p, y, r, x)];
           }
           vt[pl * 3 + o][r1][r2] = v;
           gvt[pl * 3 + o][r1][r2] = 0.0;
@@ -142,7 +142,7 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
           double v = 0.0;
           if (x < nvs && y < nvt) {
             const int p = o == 0 ? tr.j : tr.i;
-            v = a.ovov_ts[(((int64_t)tr.k * nvt + y) * nos + p) * nvs + x];
+            v = a.ovov_ts[ovts_idx(a, tr.k, y, p, x)];
           }
           vt[pl * 2 + o][r1][r2] = v;
           gvt[pl * 2 + o][r1][r2] = 0.0;
@@ -151,8 +151,8 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
       const int x = a0 + r1, y = b0 + r2;
       double v = 0.0;
       if (x < nvs && y < nvs)
-        v = a.ovov_ss[(((int64_t)tr.i * nvs + x) * nos + tr.j) * nvs + y] -
-            a.ovov_ss[(((int64_t)tr.i * nvs + y) * nos + tr.j) * nvs + x];
+        v = a.ovov_ss[ovss_idx(a, tr.i, x, tr.j, y)] -
+            a.ovov_ss[ovss_idx(a, tr.i, y, tr.j, x)];
       vt[4][r1][r2] = v;
       gvt[4][r1][r2] = 0.0;
     }
@@ -275,8 +275,8 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
           const double gk = gvt[pl * 3 + o][r1][r2];
           if (gk == 0.0) continue;
           const int p = occ3[o][0], r = occ3[o][1];
-          atomicAdd(&dov_ss[(((int64_t)p * nvs + x) * nos + r) * nvs + y], gk);
-          atomicAdd(&dov_ss[(((int64_t)p * nvs + y) * nos + r) * nvs + x], -gk);
+          atomicAdd(&dov_ss[ovss_idx(a, p, x, r, y)], gk);
+          atomicAdd(&dov_ss[ovss_idx(a, p, y, r, x)], -gk);
         }
       }
     } else {
@@ -288,14 +288,14 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
           const double gk = gvt[pl * 2 + o][r1][r2];
           if (gk == 0.0) continue;
           const int p = o == 0 ? tr.j : tr.i;
-          atomicAdd(&dov_ts[(((int64_t)tr.k * nvt + y) * nos + p) * nvs + x], gk);
+          atomicAdd(&dov_ts[ovts_idx(a, tr.k, y, p, x)], gk);
         }
       }
       const int x = a0 + r1, y = b0 + r2;
       const double gk = gvt[4][r1][r2];
       if (x < nvs && y < nvs && gk != 0.0) {
-        atomicAdd(&dov_ss[(((int64_t)tr.i * nvs + x) * nos + tr.j) * nvs + y], gk);
-        atomicAdd(&dov_ss[(((int64_t)tr.i * nvs + y) * nos + tr.j) * nvs + x], -gk);
+        atomicAdd(&dov_ss[ovss_idx(a, tr.i, x, tr.j, y)], gk);
+        atomicAdd(&dov_ss[ovss_idx(a, tr.i, y, tr.j, x)], -gk);
       }
     }
     if (tid < 3 * TB) {

@@ -48,10 +48,15 @@ struct EnergyArgs {
   const double* eps_t; // [nbas] spin t
   const double* t1s;   // [nos][nvs]
   const double* t1t;   // [not][nvt]
-  // (ia|jb) spin s-s, [nos][nvs][nos][nvs]
+  // V-term integral blocks, stored only for the occupied orbitals the computed
+  // triplets use (occupied index -> slot through oslot_s / oslot_t, -1 = absent):
+  // (ia|jb) spin s-s as [slot i][a][slot j][b], i.e. [ns_c][nvs][ns_c][nvs]
   const double* ovov_ss;
-  // mixed: (jb|KC) as [K][C][j][b] = ovov_ts[K][C][j][b], i.e. [not][nvt][nos][nvs]
+  // mixed: (jb|KC) as [slot K][C][slot j][b], i.e. [nt_c][nvt][ns_c][nvs]
   const double* ovov_ts;
+  const int* oslot_s;  // [nos]
+  const int* oslot_t;  // [not] (same spin: equal to oslot_s)
+  int ns_c, nt_c;      // number of slots
   const int3* blocks;  // cube tiles (A,B,C) of 16-blocks
   int nblocks;
   int pitch_x;         // row pitch (elements) of XT / YT (same: a; mixed: a)
@@ -61,6 +66,15 @@ struct EnergyArgs {
   const Trip* trips;   // [ntrip]
   double* partial;     // [ntrip][gridDim.x]
 };
+
+// (px|ry) of spin s in the slot-compacted [ns][nvs][ns][nvs] block
+__device__ __forceinline__ int64_t ovss_idx(const EnergyArgs& a, int p, int x, int r, int y) {
+  return (((int64_t)a.oslot_s[p] * a.nvs + x) * a.ns_c + a.oslot_s[r]) * a.nvs + y;
+}
+// (px|KC) with p of spin s, K of spin t: [nt][nvt][ns][nvs]
+__device__ __forceinline__ int64_t ovts_idx(const EnergyArgs& a, int K, int C, int p, int x) {
+  return (((int64_t)a.oslot_t[K] * a.nvt + C) * a.ns_c + a.oslot_s[p]) * a.nvs + x;
+}
 
 // Tensor-core contraction problem: up to kMaxSeg K-segments, each a row block
 // of a sliced operand tensor addressed through a TMA map (index 0 or 1).

@@ -151,8 +151,8 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
               const int p = occ3[o][0], r = occ3[o][1];
               // K^{pr}_{xy} = (px|ry) - (py|rx)
               const double* ov = a.ovov_ss;
-              double v1 = ov[(((int64_t)p * nvs + x) * nos + r) * nvs + y];
-              double v2 = ov[(((int64_t)p * nvs + y) * nos + r) * nvs + x];
+              double v1 = ov[ovss_idx(a, p, x, r, y)];
+              double v2 = ov[ovss_idx(a, p, y, r, x)];
               v = (T)(v1 - v2);
             }
             vt[pl * 3 + o][r1][r2] = v;
@@ -171,7 +171,7 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
             T v = 0;
             if (x < nvs && y < nvt) {
               const int p = o == 0 ? tr.j : tr.i;
-              v = (T)a.ovov_ts[(((int64_t)K * nvt + y) * nos + p) * nvs + x];
+              v = (T)a.ovov_ts[ovts_idx(a, K, y, p, x)];
             }
             vt[pl * 2 + o][r1][r2] = v;
           }
@@ -181,8 +181,8 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
           T v = 0;
           if (x < nvs && y < nvs) {
             const double* ov = a.ovov_ss;
-            double v1 = ov[(((int64_t)tr.i * nvs + x) * nos + tr.j) * nvs + y];
-            double v2 = ov[(((int64_t)tr.i * nvs + y) * nos + tr.j) * nvs + x];
+            double v1 = ov[ovss_idx(a, tr.i, x, tr.j, y)];
+            double v2 = ov[ovss_idx(a, tr.i, y, tr.j, x)];
             v = (T)(v1 - v2);
           }
           vt[4][r1][r2] = v;
@@ -313,8 +313,8 @@ __global__ void energy_prep(EnergyArgs a, float* __restrict__ vt_out, int64_t vt
       const int o = (int)(r / nvs);
       const int p = occ3[o][0], q = occ3[o][1];
       const double* ov = a.ovov_ss;
-      const double v1 = ov[(((int64_t)p * nvs + x) * nos + q) * nvs + y];
-      const double v2 = ov[(((int64_t)p * nvs + y) * nos + q) * nvs + x];
+      const double v1 = ov[ovss_idx(a, p, x, q, y)];
+      const double v2 = ov[ovss_idx(a, p, y, q, x)];
       out[((int64_t)o * nvs + x) * pv + y] = (float)(v1 - v2);
     }
   } else {
@@ -328,13 +328,13 @@ __global__ void energy_prep(EnergyArgs a, float* __restrict__ vt_out, int64_t vt
         const int o = (int)(r / nvs);   // 0: j, 1: i
         const int p = o == 0 ? tr.j : tr.i;
         out[((int64_t)o * nvs + x) * pvt + C] =
-            (float)a.ovov_ts[(((int64_t)tr.k * nvt + C) * nos + p) * nvs + x];
+            (float)a.ovov_ts[ovts_idx(a, tr.k, C, p, x)];
       } else {
         const int64_t q = idx - n1;
         const int y = (int)(q % nvs), x = (int)(q / nvs);
         const double* ov = a.ovov_ss;
-        const double v1 = ov[(((int64_t)tr.i * nvs + x) * nos + tr.j) * nvs + y];
-        const double v2 = ov[(((int64_t)tr.i * nvs + y) * nos + tr.j) * nvs + x];
+        const double v1 = ov[ovss_idx(a, tr.i, x, tr.j, y)];
+        const double v2 = ov[ovss_idx(a, tr.i, y, tr.j, x)];
         out[2LL * nvs * pvt + (int64_t)x * pv + y] = (float)(v1 - v2);
       }
     }

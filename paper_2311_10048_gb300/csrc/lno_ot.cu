@@ -62,6 +62,11 @@ cudaError_t launch_pack_at2(const int2*, int, int, int, int, int, int, const dou
                             const double*, St, cudaStream_t);
 cudaError_t launch_transpose_t2ab(const double*, int, int, int, int, double*, cudaStream_t);
 cudaError_t launch_absmax(const double*, int64_t, unsigned long long*, cudaStream_t);
+cudaError_t launch_gather_rows(const void* src, void* dst, const int* list, int nlist,
+                               int64_t row_bytes, int nslice, int64_t src_slice_bytes,
+                               int64_t dst_slice_bytes, cudaStream_t s);
+cudaError_t launch_scatter_add_rows(const double* src, double* dst, const int* list, int nlist,
+                                    int64_t row, cudaStream_t s);
 // tc_gemm.cu
 int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
                      int64_t slice_stride, int box_rows);
@@ -243,7 +248,6 @@ struct Run {
   int nbas, naux, no[2], nv[2];
   // DF factor blocks per spin (rows, K = naux)
   Operand Boo[2], Bov[2], Bvv[2];
-  double* ovov_ss[2] = {nullptr, nullptr};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> contract_ev, energy_ev;
   lno_ot_stats* stats;
 
@@ -375,12 +379,18 @@ struct Run {
     return LNO_OT_OK;
   }
 
-  // (ia|jb) of spin s, in the arena of the spin pass that needs it
-  int ensure_ovov(int s, Arena& ar) {
-    if (ovov_ss[s]) return LNO_OT_OK;
-    const int64_t n = (int64_t)no[s] * nv[s];
-    TRY(ar.get(&ovov_ss[s], (size_t)std::max<int64_t>(n * n, 1)));
-    TRY(df(Bov[s], 0, (int)n, Bov[s], 0, (int)n, ovov_ss[s], (int)n));
+  // dst slot q = src rows [dlist[q] * rows, (dlist[q] + 1) * rows): a DF block
+  // restricted to some occupied orbitals (same slicing and scales as src)
+  int gather_operand(Arena& ar, const Operand& src, const int* dlist, int nlist, int64_t rows,
+                     Operand& dst) {
+    TRY(alloc_operand(ar, dst, nlist, rows, src.K, Sdf));
+    if (nlist == 0 || rows == 0) return LNO_OT_OK;
+    stats->other_launches++;
+    if (f64)
+      CU(launch_gather_rows(src.f64, dst.f64, dlist, nlist, rows * src.Kp * 8, 1, 0, 0, st));
+    else
+      CU(launch_gather_rows(src.bf, dst.bf, dlist, nlist, rows * src.Kp * 2, src.S,
+                            src.slice_stride * 2, dst.slice_stride * 2, st));
     return LNO_OT_OK;
   }
 };
@@ -477,7 +487,16 @@ struct SpinPass {
   int group_cap = 64;        // triplets per group (upper bound)
   double* t2st = nullptr;    // [os][ot][vs][vt]
   const double* t2ss = nullptr;
-  double* ovov_ts = nullptr; // (jb|KC) as [ot][vt][os][vs]
+  // V-term integrals over the occupied orbitals in use: spin-s slots are those
+  // of listBT (every i, j, k of a computed triplet), spin-t slots those of
+  // listBF (every K of a mixed triplet)
+  Operand BsS, BsT;          // Bov rows of the slots, [slot][vir] x naux
+  double* ovss = nullptr;    // (ia|jb) as [nS][vs][nS][vs]
+  double* ovts = nullptr;    // (jb|KC) as [nT][vt][nS][vs]
+  int* d_slot_s = nullptr;   // occupied index -> slot (-1 absent), spin s [os]
+  int* d_slot_t = nullptr;   // spin t [ot]
+  int* d_list_s = nullptr;   // slot -> occupied index
+  int* d_list_t = nullptr;
 
   Arena own;  // operands and temporaries of this spin pass
 
@@ -626,6 +645,41 @@ struct SpinPass {
       A.drop(lT);
     }
     return LNO_OT_OK;
+  }
+
+  int upload_ints(const std::vector<int>& h, int** d) {
+    TRY(own.get(d, std::max<size_t>(h.size(), 1)));
+    if (!h.empty())
+      CU(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, R.st));
+    return LNO_OT_OK;
+  }
+
+  int build_v_blocks() {
+    const int nS = (int)listBT.size(), nT = (int)listBF.size();
+    TRY(upload_ints(slotBT, &d_slot_s));
+    TRY(upload_ints(slotBF, &d_slot_t));
+    TRY(upload_ints(listBT, &d_list_s));
+    TRY(upload_ints(listBF, &d_list_t));
+    const int64_t ns = (int64_t)nS * v;
+    TRY(R.gather_operand(own, R.Bov[s], d_list_s, nS, v, BsS));
+    TRY(own.get(&ovss, (size_t)std::max<int64_t>(ns * ns, 1)));
+    TRY(R.df(BsS, 0, (int)ns, BsS, 0, (int)ns, ovss, (int)ns));
+    if (!mixed.trips.empty()) {
+      const int64_t nt = (int64_t)nT * vt;
+      TRY(R.gather_operand(own, R.Bov[t], d_list_t, nT, vt, BsT));
+      TRY(own.get(&ovts, (size_t)std::max<int64_t>(nt * ns, 1)));
+      TRY(R.df(BsS, 0, (int)ns, BsT, 0, (int)nt, ovts, (int)ns));
+    }
+    return LNO_OT_OK;
+  }
+
+  void set_v_args(EnergyArgs& ea, bool is_mixed) const {
+    ea.ovov_ss = ovss;
+    ea.ovov_ts = ovts;
+    ea.oslot_s = d_slot_s;
+    ea.oslot_t = is_mixed ? d_slot_t : d_slot_s;
+    ea.ns_c = (int)listBT.size();
+    ea.nt_c = is_mixed ? (int)listBF.size() : ea.ns_c;
   }
 
   int prepare_inputs() {
@@ -802,8 +856,7 @@ struct SpinPass {
     ea.eps_t = R.dom->eps[is_mixed ? t : s];
     ea.t1s = R.dom->t1[s];
     ea.t1t = R.dom->t1[is_mixed ? t : s];
-    ea.ovov_ss = R.ovov_ss[s];
-    ea.ovov_ts = ovov_ts;
+    set_v_args(ea, is_mixed);
     ea.blocks = dblocks;
     ea.nblocks = (int)blocks.size();
     ea.pitch_x = P1;
@@ -932,12 +985,7 @@ struct SpinPass {
     if (same.trips.empty() && mixed.trips.empty()) return LNO_OT_OK;
     plan();
     TRY(prepare_inputs());
-    TRY(R.ensure_ovov(s, own));
-    if (!mixed.trips.empty()) {
-      const int64_t nr = (int64_t)o * v, nc = (int64_t)ot * vt;
-      TRY(own.get(&ovov_ts, (size_t)std::max<int64_t>(nr * nc, 1)));
-      TRY(R.df(R.Bov[s], 0, (int)nr, R.Bov[t], 0, (int)nc, ovov_ts, (int)nr));
-    }
+    TRY(build_v_blocks());
     TRY(build());
     TRY(run_case(false));
     TRY(run_case(true));
@@ -1017,7 +1065,6 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
     if (t1) cudaEventRecord(t1, R.st);
     TRY(pa.run());
     pa.own.release();
-    R.ovov_ss[0] = nullptr;
     TRY(pb.run());
   }
   // per-case sums
@@ -1068,7 +1115,6 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
 // Adjoint (float64).  Gradient accumulators of one domain (raw, unprojected).
 struct GradAcc {
   Operand dBoo[2], dBov[2], dBvv[2];  // same layout as the DF blocks
-  double* dovov_ss[2];
   double* dt1[2];
   double* deps[2];
   double* dt2aa;
@@ -1121,8 +1167,13 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
   TRY(zero_operand_like(A, P.BG, dBG, st));
   TRY(zero_operand_like(A, P.BF, dBF, st));
   TRY(zero_operand_like(A, P.AT2, dAT2, st));
-  double* dovov_ts = nullptr;
-  if (!P.mixed.trips.empty()) TRY(zeros(A, &dovov_ts, (int64_t)o * v * ot * vt, st));
+  // gradients of the slot-compacted V-term blocks
+  const int nS = (int)P.listBT.size(), nT = (int)P.listBF.size();
+  const int64_t ns = (int64_t)nS * v, nt = (int64_t)nT * vt;
+  double* dovss = nullptr;
+  double* dovts = nullptr;
+  TRY(zeros(A, &dovss, ns * ns, st));
+  if (!P.mixed.trips.empty()) TRY(zeros(A, &dovts, nt * ns, st));
   double* dt2ss = s == 0 ? G.dt2aa : G.dt2bb;
   double* dt2st = G.dt2ab;
   if (s == 1 && !P.mixed.trips.empty()) TRY(zeros(A, &dt2st, (int64_t)o * ot * v * vt, st));
@@ -1178,8 +1229,7 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
     ea.eps_t = R.dom->eps[is_mixed ? t : s];
     ea.t1s = R.dom->t1[s];
     ea.t1t = R.dom->t1[is_mixed ? t : s];
-    ea.ovov_ss = R.ovov_ss[s];
-    ea.ovov_ts = P.ovov_ts;
+    P.set_v_args(ea, is_mixed);
     ea.blocks = dblocks;
     ea.nblocks = (int)blocks.size();
     ea.pitch_x = P1;
@@ -1244,8 +1294,8 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
       CU(cudaMemsetAsync(dX, 0, (size_t)ng * N1 * P1 * sizeof(double), st));
       if (is_mixed) CU(cudaMemsetAsync(dZ, 0, (size_t)ng * N2 * P2 * sizeof(double), st));
       ea.trips = dtrips + g0;
-      CU(launch_energy_backward(ea, X, Z, dX, dZ, G.dt1[s], G.dt1[is_mixed ? t : s], G.dovov_ss[s],
-                                dovov_ts, G.deps[s], G.deps[is_mixed ? t : s], gE, ng, Pch, st));
+      CU(launch_energy_backward(ea, X, Z, dX, dZ, G.dt1[s], G.dt1[is_mixed ? t : s], dovss,
+                                dovts, G.deps[s], G.deps[is_mixed ? t : s], gE, ng, Pch, st));
       // contraction adjoint: dA += sign dX.B, dB += sign dX^T.A
       auto adj = [&](const std::vector<std::vector<SegRef>>& segs, const double* dXb, int64_t Nn,
                      int Mm, int ldo) -> int {
@@ -1355,9 +1405,23 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
                    o * o));
     A.drop(dlT);
   }
-  if (dovov_ts)  // (jb|KC): L = Bov_s rows (j,b), R = Bov_t rows (K,C)
-    TRY(df_adjoint(R, A, R.Bov[s], G.dBov[s], 0, o * v, R.Bov[t], G.dBov[t], 0, ot * vt, dovov_ts,
-                   o * v));
+  // V-term blocks over the gathered rows, then added back into the Bov rows:
+  // (ia|jb): L = R = BsS; (jb|KC): L = BsS rows (j,b), R = BsT rows (K,C)
+  if (nS > 0) {
+    Operand dBsS;
+    TRY(zero_operand_like(A, P.BsS, dBsS, st));
+    TRY(df_adjoint(R, A, P.BsS, dBsS, 0, (int)ns, P.BsS, dBsS, 0, (int)ns, dovss, (int)ns));
+    if (dovts && nT > 0) {
+      Operand dBsT;
+      TRY(zero_operand_like(A, P.BsT, dBsT, st));
+      TRY(df_adjoint(R, A, P.BsS, dBsS, 0, (int)ns, P.BsT, dBsT, 0, (int)nt, dovts, (int)ns));
+      CU(launch_scatter_add_rows(dBsT.f64, G.dBov[t].f64, P.d_list_t, nT, (int64_t)vt * dBsT.Kp,
+                                 st));
+      R.stats->other_launches++;
+    }
+    CU(launch_scatter_add_rows(dBsS.f64, G.dBov[s].f64, P.d_list_s, nS, (int64_t)v * dBsS.Kp, st));
+    R.stats->other_launches++;
+  }
   if (s == 1 && !P.mixed.trips.empty())
     CU(launch_adj_transpose_t2ab(dt2st, ot, o, vt, v, G.dt2ab, st));
   CU(cudaStreamSynchronize(st));
@@ -1397,7 +1461,6 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
     TRY(zero_operand_like(GA, R.Boo[s], G.dBoo[s], R.st));
     TRY(zero_operand_like(GA, R.Bov[s], G.dBov[s], R.st));
     TRY(zero_operand_like(GA, R.Bvv[s], G.dBvv[s], R.st));
-    G.dovov_ss[s] = nullptr;
     TRY(zeros(GA, &G.dt1[s], n1[s], R.st));
     TRY(zeros(GA, &G.deps[s], nbas, R.st));
   }
@@ -1423,22 +1486,10 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
     if (P.same.trips.empty() && P.mixed.trips.empty()) continue;
     P.plan();
     TRY(P.prepare_inputs());
-    TRY(R.ensure_ovov(s, P.own));
-    Arena ov_arena(R.st, 0);
-    TRY(zeros(ov_arena, &G.dovov_ss[s], n1[s] * n1[s], R.st));
-    if (!P.mixed.trips.empty()) {
-      const int64_t nr = (int64_t)P.o * P.v, nc = (int64_t)P.ot * P.vt;
-      TRY(P.own.get(&P.ovov_ts, (size_t)std::max<int64_t>(nr * nc, 1)));
-      TRY(R.df(R.Bov[s], 0, (int)nr, R.Bov[1 - s], 0, (int)nc, P.ovov_ts, (int)nr));
-    }
+    TRY(P.build_v_blocks());
     TRY(P.build());
     TRY(backward_spin(P, G, gE));
-    // (ia|jb) of spin s: L = R = Bov_s
-    TRY(df_adjoint(R, GA, R.Bov[s], G.dBov[s], 0, (int)n1[s], R.Bov[s], G.dBov[s], 0, (int)n1[s],
-                   G.dovov_ss[s], (int)n1[s]));
     CU(cudaStreamSynchronize(R.st));
-    R.ovov_ss[s] = nullptr;
-    G.dovov_ss[s] = nullptr;
   }
   // outputs: dB (symmetrised), deps, dt1, dt2 (antisymmetrised same-spin)
   for (int s = 0; s < 2; ++s) {

@@ -234,6 +234,33 @@ __global__ void absmax_kernel(const double* __restrict__ x, int64_t n,
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
+// Row-block gather: dst slot q <- src slot list[q], each slot `row16` 16-byte
+// words, repeated over `nslice` slices (bf16 slices of one operand, or one
+// float64 plane).  Used to keep only the occupied orbitals a triplet set uses.
+__global__ void gather_rows_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                   const int* __restrict__ list, int nlist, int64_t row16,
+                                   int nslice, int64_t src_slice16, int64_t dst_slice16) {
+  const int64_t per = (int64_t)nlist * row16, n = per * nslice;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = e / per, r = e - sl * per;
+    const int64_t q = r / row16, w = r - q * row16;
+    dst[sl * dst_slice16 + r] = src[sl * src_slice16 + (int64_t)list[q] * row16 + w];
+  }
+}
+
+// dst slot list[q] += src slot q (float64; slots of `row` elements, list
+// entries distinct, so no two threads touch one element).
+__global__ void scatter_add_rows_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                        const int* __restrict__ list, int nlist, int64_t row) {
+  const int64_t n = (int64_t)nlist * row;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e / row, w = e - q * row;
+    dst[(int64_t)list[q] * row + w] += src[e];
+  }
+}
+
 inline int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
@@ -313,6 +340,28 @@ cudaError_t launch_transpose_t2ab(const double* t2ab, int na, int nb, int va, in
   int64_t n = (int64_t)na * nb * va * vb;
   if (n == 0) return cudaSuccess;
   transpose_t2ab<<<grid_for(n), 256, 0, s>>>(t2ab, na, nb, va, vb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const void* src, void* dst, const int* list, int nlist,
+                               int64_t row_bytes, int nslice, int64_t src_slice_bytes,
+                               int64_t dst_slice_bytes, cudaStream_t s) {
+  if (nlist == 0 || row_bytes == 0 || nslice == 0) return cudaSuccess;
+  if (row_bytes % 16 || src_slice_bytes % 16 || dst_slice_bytes % 16 ||
+      reinterpret_cast<uintptr_t>(src) % 16 || reinterpret_cast<uintptr_t>(dst) % 16)
+    return cudaErrorInvalidValue;
+  const int64_t n = (int64_t)nlist * (row_bytes / 16) * nslice;
+  gather_rows_kernel<<<grid_for(n), 256, 0, s>>>(
+      static_cast<const uint4*>(src), static_cast<uint4*>(dst), list, nlist, row_bytes / 16,
+      nslice, src_slice_bytes / 16, dst_slice_bytes / 16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_add_rows(const double* src, double* dst, const int* list, int nlist,
+                                    int64_t row, cudaStream_t s) {
+  const int64_t n = (int64_t)nlist * row;
+  if (n == 0) return cudaSuccess;
+  scatter_add_rows_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, list, nlist, row);
   return cudaGetLastError();
 }
 
