@@ -9,8 +9,13 @@ out over spin orbitals with no spin-case algebra at all:
   <pq||rs> = <pq|rs> - <pq|sr>,  <pq|rs> = (pr|qs) delta(s_p,s_r) delta(s_q,s_s)
   W^{abc}_{ijk} = P(i/jk) P(a/bc) [ sum_e t^{ae}_{jk} <ei||bc>
                                     - sum_m t^{bc}_{im} <ma||jk> ]
-  V^{abc}_{ijk} = P(i/jk) P(a/bc) t^a_i <jk||bc>
+  V^{abc}_{ijk} = P(i/jk) P(a/bc) [ t^a_i <jk||bc> + f_ia t^{bc}_{jk} ]
   E = 1/36 sum_{ijkabc} W (W + V) / D
+
+(f_ia: the optional occupied-virtual Fock block of an RO reference, zero
+when the domain has no ``fov``.)  ``orbital_partition`` applies the
+prefactors of eq cim_pt_energy (1/36 same spin, 1/8 mixed) to these
+spin-orbital tensors.
 
 All occupied (i,j,k) and virtual (a,b,c) spin orbitals are enumerated, so the
 tensors hold n_occ^3 n_vir^3 numbers: keep nbas <= 12.
@@ -95,6 +100,18 @@ def _amplitudes(d, occ, vir):
     return t1, t2
 
 
+def _fock_ov(d, occ, vir):
+    """Spin-orbital f_ia [i][a] (zero across spins, zero without ``fov``)."""
+    f = torch.zeros(len(occ), len(vir), dtype=_f64)
+    if d.get("fov") is None:
+        return f
+    for I, (si, i) in enumerate(occ):
+        for A, (sa, a) in enumerate(vir):
+            if si == sa:
+                f[I, A] = d["fov"][si][i, a - d["nocc"][si]]
+    return f
+
+
 def _p3(x, axes):
     """P(p/qr) on three axes of x: f(pqr) - f(qpr) - f(rqp)."""
     p, q, r = axes
@@ -119,7 +136,8 @@ def brute_force(dom, return_tensors=False):
         c = torch.einsum("jkae,eibc->ijkabc", t2, ei_bc) \
             - torch.einsum("imbc,majk->ijkabc", t2, ma_jk)
         W = _p3(_p3(c, (0, 1, 2)), (3, 4, 5))
-        v = torch.einsum("ia,jkbc->ijkabc", t1, jk_bc)
+        v = torch.einsum("ia,jkbc->ijkabc", t1, jk_bc) \
+            + torch.einsum("ia,jkbc->ijkabc", _fock_ov(d, occ, vir), t2)
         V = _p3(_p3(v, (0, 1, 2)), (3, 4, 5))
         eo = torch.stack([d["eps"][s][p] for s, p in occ])
         ev = torch.stack([d["eps"][s][p] for s, p in vir])
@@ -134,5 +152,35 @@ def brute_force(dom, return_tensors=False):
             out[name] = float(E[nbeta == nb_].sum())
         out["total"] = float(E.sum())
         if return_tensors:
-            return out, dict(W=W, V=V, occ=occ, vir=vir)
+            return out, dict(W=W, V=V, D=D, occ=occ, vir=vir)
         return out
+
+
+def orbital_partition(dom):
+    """Orbital contributions written out from eq cim_pt_energy over spin
+    orbitals: for an occupied orbital p of spin s (t the other spin),
+
+      dE_p = 1/36 sum_{jk abc, all spin s} E6[p,j,k,a,b,c]
+           + 1/8 sum_{a (s); J,K,B,C (t)} E6[p,J,K,a,B,C]
+           + 1/8 sum_{j,a,b (s); K,C (t)} E6[p,j,K,a,b,C]
+
+    with E6 = W (W + V) / D over unrestricted spin-orbital indices.
+    Returns {"alpha": [...], "beta": [...]} (floats).
+    """
+    d = dom if isinstance(dom["B"][0], torch.Tensor) else as_tensors(dom)
+    _, t = brute_force(d, return_tensors=True)
+    with torch.no_grad():
+        E6 = t["W"] * (t["W"] + t["V"]) / t["D"]
+        occ, vir = t["occ"], t["vir"]
+        os_ = torch.tensor([s for s, _ in occ])
+        vs_ = torch.tensor([s for s, _ in vir])
+        res = {"alpha": [], "beta": []}
+        for I, (s, p) in enumerate(occ):
+            o_s, o_t = os_ == s, os_ != s
+            v_s, v_t = vs_ == s, vs_ != s
+            e = E6[I]                                        # [j][k][a][b][c]
+            same = e[o_s][:, o_s][:, :, v_s][:, :, :, v_s][:, :, :, :, v_s].sum() / 36.0
+            two_t = e[o_t][:, o_t][:, :, v_s][:, :, :, v_t][:, :, :, :, v_t].sum() / 8.0
+            one_t = e[o_s][:, o_t][:, :, v_s][:, :, :, v_s][:, :, :, :, v_t].sum() / 8.0
+            res["alpha" if s == 0 else "beta"].append(float(same + two_t + one_t))
+        return res

@@ -14,7 +14,7 @@ out literally):
 
   W^{abc}_{ijk} = P(i/jk) P(a/bc) [ sum_e t^{ae}_{jk} <ei||bc>
                                     - sum_m t^{bc}_{im} <ma||jk> ]
-  V^{abc}_{ijk} = P(i/jk) P(a/bc) t^a_i <jk||bc>
+  V^{abc}_{ijk} = P(i/jk) P(a/bc) [ t^a_i <jk||bc> + f_ia t^{bc}_{jk} ]
   E(T) = 1/36 sum_{ijkabc} W (W + V) / D,  D = e_i+e_j+e_k-e_a-e_b-e_c
 
 with P(i/jk) f(ijk) = f(ijk) - f(jik) - f(kji).  This module evaluates the
@@ -23,8 +23,20 @@ same spin i<j<k with a<b<c, mixed spin i<j (spin s), K (spin t) with
 a<b (s), C (t).  Mulliken integrals come from the DF factors,
 (pq|rs) = sum_Q B^Q_pq B^Q_rs (Sec. 3.2, eq ed_df_int with B = I L^-T).
 
+The f_ia term is the restricted open-shell one: with an RO reference the
+semicanonical Fock matrix keeps an occupied-virtual block (Sec. 3.3, eq
+off_diagonal_fock and the singles of eq cim_mp2_ed_energy); it enters V the
+way t^a_i does, with the doubles amplitude in place of the integral.  It is
+optional (``fov`` absent or None means zero).
+
+Orbital contributions (eq cim_pt_energy): E(T) = sum_i dE_i + sum_I dE_I with
+1/36 on the same-spin sum and 1/8 on each mixed sum over unrestricted
+indices.  Per restricted triplet that gives each orbital of a same-spin
+triplet 1/3 of e_t, and in a mixed triplet 1/4 to each of the two orbitals of
+the same spin and 1/2 to the third (``orbital_energies``).
+
 Conventions (readings of the paper, listed in the design notes):
-* V carries only the T1 term (no ROHF f_ov term); E = sum W (W+V)/D.
+* E = sum W (W+V)/D with the T1 term (and the f_ov term when given) in V.
 * The full domain energy over all occupied orbitals is computed (not the
   central-LMO share of eq local_pt).
 * Triplet enumeration order (also the order of per-triplet outputs):
@@ -52,7 +64,9 @@ def as_tensors(dom, requires_grad=False):
                 B=[t(dom["B"][0]), t(dom["B"][1])],
                 eps=[t(dom["eps"][0]), t(dom["eps"][1])],
                 t1=[t(dom["t1"][0]), t(dom["t1"][1])],
-                t2aa=t(dom["t2aa"]), t2bb=t(dom["t2bb"]), t2ab=t(dom["t2ab"]))
+                t2aa=t(dom["t2aa"]), t2bb=t(dom["t2bb"]), t2ab=t(dom["t2ab"]),
+                fov=(None if dom.get("fov") is None
+                     else [t(dom["fov"][0]), t(dom["fov"][1])]))
 
 
 def triplets(case, na, nb):
@@ -113,6 +127,7 @@ class Evaluator:
         # t2st[s] = t^{a C}_{i K} with i,a of spin s and K,C of the other spin
         self.t2st = [d["t2ab"], d["t2ab"].permute(1, 0, 3, 2)]
         self.t1 = d["t1"]
+        self.fov = d.get("fov")        # None or [f_ia spin up, f_IA spin down]
         self._cache = {}
 
     def _c(self, key, fn):
@@ -155,9 +170,14 @@ class Evaluator:
             - self._z_same(s, k, j, i)
         W = X - X.permute(1, 0, 2) - X.permute(2, 1, 0)
         t1 = self.t1[s]
+        fv = None if self.fov is None else self.fov[s]
 
         def y(p, q, r):
-            return t1[p][:, None, None] * self._kbar(s, q, r)[None, :, :]
+            # t^a_p <qr||bc>  (+ f_pa t^{bc}_{qr})
+            out = t1[p][:, None, None] * self._kbar(s, q, r)[None, :, :]
+            if fv is not None:
+                out = out + fv[p][:, None, None] * self.t2ss[s][q, r][None, :, :]
+            return out
         Yb = y(i, j, k) - y(j, i, k) - y(k, j, i)
         V = Yb - Yb.permute(1, 0, 2) - Yb.permute(2, 1, 0)
         return W, V
@@ -215,6 +235,13 @@ class Evaluator:
         u = t1s[i][:, None, None] * kjb[None] - t1s[j][:, None, None] * kib[None]
         oo = _eri(Ss, i, Ss.v, Ss, j, Ss.v)                   # (ia|jb) [a][b]
         V = u - u.permute(1, 0, 2) + t1t[K][None, None, :] * (oo - oo.T)[:, :, None]
+        if self.fov is not None:
+            # the same terms with t^x_p -> f_px and the integral -> the doubles
+            # amplitude of the same indices: (jb|KC) -> t^{bC}_{jK},
+            # (ia|jb) - (ib|ja) -> t^{ab}_{ij}
+            fs, ft = self.fov[s], self.fov[t]
+            uf = fs[i][:, None, None] * tst[j, K][None] - fs[j][:, None, None] * tst[i, K][None]
+            V = V + uf - uf.permute(1, 0, 2) + ft[K][None, None, :] * tss[i, j][:, :, None]
         return W, V
 
     def mixed_energy(self, s, i, j, K):
@@ -269,6 +296,40 @@ def triplet_energies(dom, case, trips=None):
     ev = Evaluator(dom)
     with torch.no_grad():
         return [float(e) for e in ev.case_energies(case, trips)]
+
+
+def orbital_energies(dom, trip_sel=None):
+    """Orbital contributions dE_i (spin up) and dE_I (spin down) of eq
+    cim_pt_energy, from the per-triplet contributions: same-spin triplet
+    1/3 to each orbital; mixed triplet 1/4 to each of its two same-spin
+    orbitals and 1/2 to the other.  ``trip_sel`` (dict case -> list of
+    triplet indices) restricts the sums to those triplets.
+
+    Returns {"alpha": [na floats], "beta": [nb floats]}, each summed with
+    math.fsum.
+    """
+    ev = Evaluator(dom)
+    na, nb = ev.d["nocc"]
+    parts = {0: [[] for _ in range(na)], 1: [[] for _ in range(nb)]}
+    with torch.no_grad():
+        for c in CASES:
+            allt = triplets(c, na, nb)
+            idx = range(len(allt)) if trip_sel is None or trip_sel.get(c) is None \
+                else trip_sel[c]
+            for q in idx:
+                i, j, k = allt[q]
+                e = float(ev.triplet_energy(c, (i, j, k)))
+                if c in ("aaa", "bbb"):
+                    s = 0 if c == "aaa" else 1
+                    for p in (i, j, k):
+                        parts[s][p].append(e / 3.0)
+                else:
+                    s = 0 if c == "aab" else 1
+                    parts[s][i].append(e / 4.0)
+                    parts[s][j].append(e / 4.0)
+                    parts[1 - s][k].append(e / 2.0)
+    return {"alpha": [math.fsum(x) for x in parts[0]],
+            "beta": [math.fsum(x) for x in parts[1]]}
 
 
 def energy_graph(dom_t):

@@ -118,6 +118,22 @@ def make_domain(nbas, nocc, naux, L, seed, t1_sd=1e-3, closed_shell=False):
                 t1=[t1a, t1b], **mp2_like_t2(Ba, ea, na, Bb, eb, nb))
 
 
+def add_fov(dom, sd=0.02, seed=0):
+    """Copy of ``dom`` with an off-diagonal Fock block per spin.
+
+    ``fov[s]`` [nocc[s]][nvir[s]] ~ N(0, sd), drawn from a generator of its
+    own (PCG64 seeded with (seed, 7)) so that every other input of the domain
+    stays bit for bit what ``make_domain`` gave.  Stands in for the f_ia of a
+    restricted open-shell reference in the semicanonical basis.
+    """
+    rng = np.random.default_rng([int(seed), 7])
+    na, nb = dom["nocc"]
+    n = dom["nbas"]
+    out = dict(dom)
+    out["fov"] = [rng.normal(0.0, sd, size=(na, n - na)), rng.normal(0.0, sd, size=(nb, n - nb))]
+    return out
+
+
 def mp2_like_t2(Ba, ea, na, Bb, eb, nb):
     """MP2-like doubles from B and eps (input recipe, see module docstring).
 

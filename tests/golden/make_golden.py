@@ -5,10 +5,12 @@ Calls only ``oracle`` (and the seeded input generator).  Usage:
     python tests/golden/make_golden.py c0        # all triplets, seconds
     python tests/golden/make_golden.py c4        # all triplets, ~1-2 h CPU
     python tests/golden/make_golden.py c1s       # seeded triplet sample of c1
+    python tests/golden/make_golden.py c0f       # c0 plus an f_ov block (add_fov)
 
 Each output file holds the configuration, the per-triplet contributions e_t
 (in the oracle's triplet order, or with explicit indices for samples) and the
-per-case sums (math.fsum).
+per-case sums (math.fsum); full runs also hold the orbital contributions
+of eq cim_pt_energy (``orbital``: alpha and beta lists).
 """
 from __future__ import annotations
 
@@ -23,8 +25,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-from oracle.triples import CASES, Evaluator, triplets  # noqa: E402
-from paper_2311_10048_gb300.synth import CONFIGS, config_domain  # noqa: E402
+from oracle.triples import CASES, Evaluator, orbital_energies, triplets  # noqa: E402
+from paper_2311_10048_gb300.synth import CONFIGS, add_fov, config_domain  # noqa: E402
+
+FOV_SD, FOV_SEED = 0.02, 0
 
 SAMPLE_SEED = 20231110
 SAMPLE_PER_CASE = 6
@@ -44,11 +48,15 @@ def sample_indices(case, na, nb, k=SAMPLE_PER_CASE, seed=SAMPLE_SEED):
 def run(name):
     import torch
     torch.set_num_threads(int(os.environ.get("ORACLE_THREADS", os.cpu_count())))
-    cfg = name[:-1] if name.endswith("s") else name
+    cfg = name[:-1] if name.endswith(("s", "f")) else name
     d = config_domain(cfg)
+    if name.endswith("f"):
+        d = add_fov(d, sd=FOV_SD, seed=FOV_SEED)
     na, nb = d["nocc"]
     ev = Evaluator(d)
     out = dict(config=cfg, params=CONFIGS[cfg], cases={})
+    if name.endswith("f"):
+        out["fov"] = dict(sd=FOV_SD, seed=FOV_SEED)
     t0 = time.time()
     with torch.no_grad():
         for case in CASES:
@@ -63,6 +71,7 @@ def run(name):
             print(name, case, len(e), time.time() - t0, flush=True)
     if not name.endswith("s"):
         out["total"] = math.fsum(out["cases"][c]["sum"] for c in CASES)
+        out["orbital"] = orbital_energies(d)
     out["oracle_seconds"] = time.time() - t0
     path = os.path.join(HERE, f"{name}_energy.json")
     with open(path, "w") as f:

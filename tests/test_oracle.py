@@ -267,3 +267,119 @@ def test_planted_oracle_mistakes_are_caught_by_brute_force(mistake):
     with _Planted(attr, mk):
         bad = T.energy(d)
     assert not close(bad["aaa"], ref["aaa"], rel=1e-9)
+
+
+# ---- restricted open-shell f_ov term and orbital contributions --------------
+from oracle.spinorbital import orbital_partition
+from paper_2311_10048_gb300.synth import add_fov
+
+FOV_SHAPES = [(9, 3, 2, 1), (10, 4, 4, 2), (8, 3, 1, 4), (9, 4, 2, 6), (7, 2, 2, 7)]
+
+
+@pytest.mark.parametrize("shape", FOV_SHAPES)
+def test_fov_spin_cases_equal_spin_orbital_brute_force(shape):
+    d = add_fov(tiny(*shape), sd=0.05, seed=shape[-1])
+    e, b = T.energy(d), brute_force(d)
+    for k in CASES + ("total",):
+        assert close(e[k], b[k]), (k, e[k], b[k])
+    # the term is not a no-op on these inputs
+    assert not close(e["total"], T.energy(tiny(*shape))["total"], rel=1e-9)
+
+
+def test_fov_enters_affinely_with_t1():
+    # V is linear in (t1, f) and E is affine in V:
+    # E(t1, f) - E(0, 0) = [E(t1, 0) - E(0, 0)] + [E(0, f) - E(0, 0)]
+    base = tiny(9, 3, 2, 41)
+    f = add_fov(base, sd=0.05, seed=41)["fov"]
+    z1 = [np.zeros_like(x) for x in base["t1"]]
+    e = lambda t1, fov: T.energy(dict(base, t1=t1, fov=fov))["total"]
+    e00, e10, e01, e11 = e(z1, None), e(base["t1"], None), e(z1, f), e(base["t1"], f)
+    assert close(e11 - e00, (e10 - e00) + (e01 - e00), rel=1e-10)
+    # zero block == no block
+    assert e(base["t1"], [np.zeros_like(x) for x in f]) == e10
+    # and the f part scales linearly
+    e02 = e(z1, [2 * x for x in f])
+    assert close(e02 - e00, 2 * (e01 - e00), rel=1e-10)
+
+
+@pytest.mark.parametrize("shape", FOV_SHAPES[:3])
+@pytest.mark.parametrize("with_fov", [False, True])
+def test_orbital_energies_equal_eq_prefactor_sums(shape, with_fov):
+    d = tiny(*shape)
+    if with_fov:
+        d = add_fov(d, sd=0.05, seed=shape[-1])
+    o, ob = T.orbital_energies(d), orbital_partition(d)
+    for s in ("alpha", "beta"):
+        assert len(o[s]) == len(ob[s])
+        for x, y in zip(o[s], ob[s]):
+            assert close(x, y, rel=1e-11, abs_=1e-14), (s, x, y)
+    assert close(math.fsum(o["alpha"] + o["beta"]), T.energy(d)["total"], rel=1e-12)
+
+
+def test_orbital_energies_follow_relabelling():
+    d = tiny(9, 4, 2, 51)
+    perm = np.array([2, 0, 3, 1])                # spin-up occupied relabelling
+    p = dict(d)
+    na = d["nocc"][0]
+    full = np.concatenate([perm, np.arange(na, d["nbas"])])
+    p["B"] = [d["B"][0][:, full][:, :, full], d["B"][1]]
+    p["eps"] = [d["eps"][0][full], d["eps"][1]]
+    p["t1"] = [d["t1"][0][perm], d["t1"][1]]
+    p["t2aa"] = d["t2aa"][perm][:, perm]
+    p["t2ab"] = d["t2ab"][perm]
+    o, op = T.orbital_energies(d), T.orbital_energies(p)
+    for q in range(na):
+        assert close(op["alpha"][q], o["alpha"][perm[q]], rel=1e-11)
+    for q in range(d["nocc"][1]):
+        assert close(op["beta"][q], o["beta"][q], rel=1e-11)
+
+
+@pytest.mark.parametrize("mistake", ["fov_mixed_sign", "fov_same_swap"])
+def test_planted_fov_mistakes_are_caught_by_brute_force(mistake):
+    d = add_fov(tiny(9, 3, 2, 93), sd=0.05, seed=93)
+    ref = brute_force(d)
+    if mistake == "fov_mixed_sign":
+        def mk(old):
+            def wv(self, s, i, j, K):
+                W, V = old(self, s, i, j, K)
+                # undo the f_KC term and add it with the wrong sign
+                ft, tss = self.fov[1 - s], self.t2ss[s]
+                return W, V - 2 * ft[K][None, None, :] * tss[i, j][:, :, None]
+            return wv
+        attr, case = "mixed_wv", "aab"
+    else:
+        def mk(old):
+            def wv(self, s, i, j, k):
+                W, V = old(self, s, i, j, k)
+                fv, t2 = self.fov[s], self.t2ss[s]
+                # replace f_pa t^{bc}_{qr} by f_pa t^{cb}_{qr} for p = i
+                delta = fv[i][:, None, None] * (t2[j, k] - t2[j, k].T)[None]
+                Y = -delta
+                return W, V + Y - Y.permute(1, 0, 2) - Y.permute(2, 1, 0)
+            return wv
+        attr, case = "same_spin_wv", "aaa"
+    with _Planted(attr, mk):
+        bad = T.energy(d)
+    assert not close(bad[case], ref[case], rel=1e-9)
+
+
+def test_planted_partition_mistake_is_caught():
+    # an equal 1/3 split of mixed triplets is a valid-looking partition that
+    # sums to the total, but not the one eq cim_pt_energy defines
+    d = tiny(9, 3, 2, 95)
+    ob = orbital_partition(d)
+    ev = T.Evaluator(d)
+    na, nb = d["nocc"]
+    eq = {"alpha": [0.0] * na, "beta": [0.0] * nb}
+    with torch.no_grad():
+        for c in CASES:
+            s = 0 if c in ("aaa", "aab") else 1
+            for (i, j, k) in T.triplets(c, na, nb):
+                e = float(ev.triplet_energy(c, (i, j, k)))
+                key = "alpha" if s == 0 else "beta"
+                other = "beta" if s == 0 else "alpha"
+                eq[key][i] += e / 3
+                eq[key][j] += e / 3
+                eq[key if c in ("aaa", "bbb") else other][k] += e / 3
+    worst = max(abs(x - y) for s in ("alpha", "beta") for x, y in zip(eq[s], ob[s]))
+    assert worst > 1e-6 * max(abs(x) for x in ob["alpha"] + ob["beta"])
