@@ -5,10 +5,11 @@
  * natural orbital domain (one "local interacting subspace", LIS) from
  * semicanonical high-spin orbitals: arXiv 2311.10048, Sec. 2.1, eq
  * cim_pt_energy, evaluated over restricted occupied triplets in the four spin
- * cases aaa, aab, abb, bbb, with the T1 (disconnected) term:
+ * cases aaa, aab, abb, bbb, with the disconnected term V:
  *
  *   E(T) = sum_cases sum_{restricted ijk} sum_{restricted abc} W (W + V) / D,
- *   W = t D (connected triples times denominator), V from T1 and <jk||bc>,
+ *   W = t D (connected triples times denominator), V from T1 and <jk||bc>
+ *   (plus f_ia and the doubles when the domain carries an f_ov block),
  *   D = e_i + e_j + e_k - e_a - e_b - e_c.
  *
  * Restricted ranges: aaa/bbb i<j<k and a<b<c; aab i<j (alpha), K (beta),
@@ -99,7 +100,15 @@ typedef struct {
  * High spin: 0 <= nocc[1] <= nocc[0] <= nbas.
  *
  * Optional:
- *   fov[s]        must be NULL (the ROHF f_ov term is not part of this path).
+ *   fov[s]        [nocc[s]][nvir[s]] f_ia: the occupied-virtual block of the
+ *                 Fock matrix in the semicanonical basis, non-zero for a
+ *                 restricted open-shell reference (Sec. 3.3, eq
+ *                 off_diagonal_fock).  It adds the disconnected term
+ *                 P(i/jk) P(a/bc) f_ia t^{bc}_{jk} to V (the T1 term with
+ *                 f_ia for t^a_i and the doubles amplitude for <jk||bc>).
+ *                 NULL for both spins = no such term; a NULL spin next to a
+ *                 non-NULL one counts as zero.  lno_ot_backward returns
+ *                 LNO_OT_EUNSUPPORTED when either is given.
  *   e_trip[c]     device float64 output, one value per computed triplet of
  *                 case c (0 aaa, 1 aab, 2 abb, 3 bbb): the triplet's
  *                 contribution sum_{restricted abc} W (W + V) / D.  NULL = not
@@ -109,7 +118,13 @@ typedef struct {
  *                 aaa (i,j,k), aab (i,j,K), abb (I,J,k), bbb (I,J,K));
  *                 NULL = all triplets.  Only the selected triplets are
  *                 computed and summed; e_trip[c][q] belongs to trip_sel[c][q].
- *   n_sel[c]      length of trip_sel[c] (ignored when it is NULL).        */
+ *   n_sel[c]      length of trip_sel[c] (ignored when it is NULL).
+ *   e_orb[s]      device float64 output [nocc[s]]: the orbital contributions
+ *                 dE_i / dE_I of eq cim_pt_energy (E(T) = sum_i dE_i +
+ *                 sum_I dE_I), i.e. 1/3 of each same-spin triplet to each of
+ *                 its orbitals, and of each mixed triplet 1/4 to each of its
+ *                 two same-spin orbitals and 1/2 to the third; over the
+ *                 computed (selected) triplets only.  NULL = not requested. */
 typedef struct {
   int nbas, naux, nocc[2];
   const double* B[2];
@@ -122,6 +137,7 @@ typedef struct {
   double* e_trip[4];
   const int64_t* trip_sel[4];
   int64_t n_sel[4];
+  double* e_orb[2];
 } lno_ot_domain;
 
 /* e = {aaa, aab, abb, bbb, total} in Eh; status as lno_ot_status. */

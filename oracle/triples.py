@@ -65,8 +65,20 @@ def as_tensors(dom, requires_grad=False):
                 eps=[t(dom["eps"][0]), t(dom["eps"][1])],
                 t1=[t(dom["t1"][0]), t(dom["t1"][1])],
                 t2aa=t(dom["t2aa"]), t2bb=t(dom["t2bb"]), t2ab=t(dom["t2ab"]),
-                fov=(None if dom.get("fov") is None
-                     else [t(dom["fov"][0]), t(dom["fov"][1])]))
+                fov=_fov_tensors(dom, t))
+
+
+def _fov_tensors(dom, t):
+    """[f spin up, f spin down] or None; a None spin block is zero."""
+    f = dom.get("fov")
+    if f is None:
+        return None
+    n = int(dom["nbas"])
+    out = []
+    for s in (0, 1):
+        o = int(dom["nocc"][s])
+        out.append(t(f[s]) if f[s] is not None else t(torch.zeros(o, n - o, dtype=_f64)))
+    return out
 
 
 def triplets(case, na, nb):

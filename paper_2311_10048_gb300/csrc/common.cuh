@@ -57,6 +57,13 @@ struct EnergyArgs {
   const int* oslot_s;  // [nos]
   const int* oslot_t;  // [not] (same spin: equal to oslot_s)
   int ns_c, nt_c;      // number of slots
+  // Source of V.  vmode 0: coefficients t1s/t1t, planes from the integral
+  // blocks above, the kernels sum W (W + V) / D.  vmode 1 (the restricted
+  // open-shell f_ov term): t1s/t1t point at the f_ov blocks, the planes are
+  // the doubles amplitudes of the same indices, and the kernels sum W V / D.
+  int vmode;
+  const double* t2ss;  // [nos][nos][nvs][nvs] t^{xy}_{pr} (vmode 1)
+  const double* t2st;  // [nos][not][nvs][nvt] t^{xC}_{pK} (vmode 1, mixed)
   const int3* blocks;  // cube tiles (A,B,C) of 16-blocks
   int nblocks;
   int pitch_x;         // row pitch (elements) of XT / YT (same: a; mixed: a)
@@ -74,6 +81,27 @@ __device__ __forceinline__ int64_t ovss_idx(const EnergyArgs& a, int p, int x, i
 // (px|KC) with p of spin s, K of spin t: [nt][nvt][ns][nvs]
 __device__ __forceinline__ int64_t ovts_idx(const EnergyArgs& a, int K, int C, int p, int x) {
   return (((int64_t)a.oslot_t[K] * a.nvt + C) * a.ns_c + a.oslot_s[p]) * a.nvs + x;
+}
+
+// Inputs of the orbital partition: per-case triplets and contributions.
+struct OrbPartArgs {
+  const double* e[4];   // per-triplet contributions of cases aaa, aab, abb, bbb
+  const Trip* trips[4];
+  int64_t n[4];
+  int na, nb;
+  double* out[2];       // [na], [nb] (either may be NULL)
+};
+
+// V plane on two spin-s virtuals: vmode 0 <pr||xy> = (px|ry) - (py|rx),
+// vmode 1 t^{xy}_{pr}
+__device__ __forceinline__ double vplane_ss(const EnergyArgs& a, int p, int x, int r, int y) {
+  if (a.vmode) return a.t2ss[(((int64_t)p * a.nos + r) * a.nvs + x) * a.nvs + y];
+  return a.ovov_ss[ovss_idx(a, p, x, r, y)] - a.ovov_ss[ovss_idx(a, p, y, r, x)];
+}
+// V plane on a spin-s and a spin-t virtual: vmode 0 (px|KC), vmode 1 t^{xC}_{pK}
+__device__ __forceinline__ double vplane_ts(const EnergyArgs& a, int K, int C, int p, int x) {
+  if (a.vmode) return a.t2st[(((int64_t)p * a.not_ + K) * a.nvs + x) * a.nvt + C];
+  return a.ovov_ts[ovts_idx(a, K, C, p, x)];
 }
 
 // Tensor-core contraction problem: up to kMaxSeg K-segments, each a row block

@@ -72,7 +72,7 @@ __device__ __forceinline__ void load_row16<double>(double* dst, const double* sr
   }
 }
 
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, bool FM>
 __global__ void __launch_bounds__(256)
 energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -149,11 +149,7 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
             T v = 0;
             if (x < nvs && y < nvs) {
               const int p = occ3[o][0], r = occ3[o][1];
-              // K^{pr}_{xy} = (px|ry) - (py|rx)
-              const double* ov = a.ovov_ss;
-              double v1 = ov[ovss_idx(a, p, x, r, y)];
-              double v2 = ov[ovss_idx(a, p, y, r, x)];
-              v = (T)(v1 - v2);
+              v = (T)vplane_ss(a, p, x, r, y);   // K^{pr}_{xy} (or t^{xy}_{pr})
             }
             vt[pl * 3 + o][r1][r2] = v;
           }
@@ -171,7 +167,7 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
             T v = 0;
             if (x < nvs && y < nvt) {
               const int p = o == 0 ? tr.j : tr.i;
-              v = (T)a.ovov_ts[ovts_idx(a, K, y, p, x)];
+              v = (T)vplane_ts(a, K, y, p, x);
             }
             vt[pl * 2 + o][r1][r2] = v;
           }
@@ -179,12 +175,7 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
         {  // plane 4: (ia|jb) - (ib|ja) on (A,B)
           const int x = a0 + r1, y = b0 + r2;
           T v = 0;
-          if (x < nvs && y < nvs) {
-            const double* ov = a.ovov_ss;
-            double v1 = ov[ovss_idx(a, tr.i, x, tr.j, y)];
-            double v2 = ov[ovss_idx(a, tr.i, y, tr.j, x)];
-            v = (T)(v1 - v2);
-          }
+          if (x < nvs && y < nvs) v = (T)vplane_ss(a, tr.i, x, tr.j, y);
           vt[4][r1][r2] = v;
         }
         (void)nt;
@@ -242,7 +233,7 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
                   t1s[6][cl] * vt[4][al][bl];
             }
             const double D = dbc - ev[0][al];
-            acc += w * (w + v) / D;
+            acc += (FM ? w * v : w * (w + v)) / D;
           }
         } else {
           const TwoF dd = split_df(dbc);
@@ -266,7 +257,7 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
                   t1s[3][bl] * vt[2][al][cl] + t1s[4][bl] * vt[3][al][cl] +
                   t1s[6][cl] * vt[4][al][bl];
             }
-            const float num = __fmul_rn(w, __fadd_rn(w, v));
+            const float num = FM ? __fmul_rn(w, v) : __fmul_rn(w, __fadd_rn(w, v));
             const float D = df_sub_round(dd, split_df(ev[0][al]));
             part = __fadd_rn(part, __fdiv_rn(num, D));
           }
@@ -312,10 +303,7 @@ __global__ void energy_prep(EnergyArgs a, float* __restrict__ vt_out, int64_t vt
       const int x = (int)(r % nvs);
       const int o = (int)(r / nvs);
       const int p = occ3[o][0], q = occ3[o][1];
-      const double* ov = a.ovov_ss;
-      const double v1 = ov[ovss_idx(a, p, x, q, y)];
-      const double v2 = ov[ovss_idx(a, p, y, q, x)];
-      out[((int64_t)o * nvs + x) * pv + y] = (float)(v1 - v2);
+      out[((int64_t)o * nvs + x) * pv + y] = (float)vplane_ss(a, p, x, q, y);
     }
   } else {
     const int64_t n1 = 2LL * nvs * nvt, n2 = (int64_t)nvs * nvs;
@@ -327,15 +315,11 @@ __global__ void energy_prep(EnergyArgs a, float* __restrict__ vt_out, int64_t vt
         const int x = (int)(r % nvs);
         const int o = (int)(r / nvs);   // 0: j, 1: i
         const int p = o == 0 ? tr.j : tr.i;
-        out[((int64_t)o * nvs + x) * pvt + C] =
-            (float)a.ovov_ts[ovts_idx(a, tr.k, C, p, x)];
+        out[((int64_t)o * nvs + x) * pvt + C] = (float)vplane_ts(a, tr.k, C, p, x);
       } else {
         const int64_t q = idx - n1;
         const int y = (int)(q % nvs), x = (int)(q / nvs);
-        const double* ov = a.ovov_ss;
-        const double v1 = ov[ovss_idx(a, tr.i, x, tr.j, y)];
-        const double v2 = ov[ovss_idx(a, tr.i, y, tr.j, x)];
-        out[2LL * nvs * pvt + (int64_t)x * pv + y] = (float)(v1 - v2);
+        out[2LL * nvs * pvt + (int64_t)x * pv + y] = (float)vplane_ss(a, tr.i, x, tr.j, y);
       }
     }
   }
@@ -375,7 +359,7 @@ __device__ __forceinline__ float div_nr(float num, float D) {
 //   T1[b][c][a] pitch 20 (float4 along a)   X[a,(bc)] / Y[a,(bC)]
 //   T2[a][c][b] pitch 18 (float2 along b)   X[b,(ac)] / Y[b,(aC)]
 //   T3[a][b][c] pitch 24                    X[c,(ab)] / Z'[C,(ab)]
-template <bool MIXED>
+template <bool MIXED, bool FM>
 __global__ void __launch_bounds__(256, 2)
 energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ Z,
            const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt) {
@@ -588,7 +572,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
                     v = da.x * k0[sb] - da.y * k1[sb] - tb0[sb] * vac.x + tb1[sb] * vac.y +
                         tc0 * vab.x;
                   }
-                  const float num = __fmul_rn(w, __fadd_rn(w, v));
+                  const float num = FM ? __fmul_rn(w, v) : __fmul_rn(w, __fadd_rn(w, v));
                   float s, e;
                   two_sum(dbc[sb].hi, -da.w, s, e);
                   const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc[sb].lo, del)));
@@ -618,19 +602,73 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   }
 }
 
-// e_trip[g] = sum_p partial[g][p] (Neumaier), one thread per triplet.
-__global__ void reduce_partials(const double* __restrict__ partial, int np, int ntrip,
+// e_trip[g] = sum_p partial[g][p] (+ sum_p partial2[g][p] when given),
+// Neumaier in a fixed order, one thread per triplet.
+__global__ void reduce_partials(const double* __restrict__ partial, int np,
+                                const double* __restrict__ partial2, int ntrip,
                                 double* __restrict__ e_trip) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ntrip) return;
   double s = 0.0, c = 0.0;
-  for (int p = 0; p < np; ++p) {
-    double x = partial[(int64_t)g * np + p];
-    double t = s + x;
-    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
-    s = t;
+  for (int half = 0; half < (partial2 ? 2 : 1); ++half) {
+    const double* src = half ? partial2 : partial;
+    for (int p = 0; p < np; ++p) {
+      double x = src[(int64_t)g * np + p];
+      double t = s + x;
+      c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
   }
   e_trip[g] = s + c;
+}
+
+// Orbital contributions of eq cim_pt_energy from per-triplet contributions:
+// same-spin triplet 1/3 to each of its orbitals; mixed triplet 1/4 to each of
+// its two same-spin orbitals and 1/2 to the third.  One CTA per occupied
+// orbital (spin up first), fixed-order Neumaier sums: bitwise reproducible.
+__global__ void orbital_partition(OrbPartArgs A) {
+  __shared__ double ss[256], cc[256];
+  const int b = blockIdx.x;
+  const int s = b < A.na ? 0 : 1;
+  const int p = s == 0 ? b : b - A.na;
+  double acc = 0.0, comp = 0.0;
+  auto add = [&](double x) {
+    double t = acc + x;
+    comp += fabs(acc) >= fabs(x) ? (acc - t) + x : (x - t) + acc;
+    acc = t;
+  };
+  for (int c = 0; c < 4; ++c) {
+    const Trip* tr = A.trips[c];
+    const double* e = A.e[c];
+    // case c: 0 aaa, 1 aab (i,j up; K down), 2 abb (I,J down; k up), 3 bbb
+    const int pair_spin = (c == 0 || c == 1) ? 0 : 1;
+    const bool same = c == 0 || c == 3;
+    for (int64_t q = threadIdx.x; q < A.n[c]; q += blockDim.x) {
+      const Trip t = tr[q];
+      if (same) {
+        if (s == pair_spin && (t.i == p || t.j == p || t.k == p)) add(e[q] / 3.0);
+      } else if (s == pair_spin) {
+        if (t.i == p || t.j == p) add(e[q] * 0.25);
+      } else if (t.k == p) {
+        add(e[q] * 0.5);
+      }
+    }
+  }
+  ss[threadIdx.x] = acc;
+  cc[threadIdx.x] = comp;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, C = 0.0;
+    for (int q = 0; q < (int)blockDim.x; ++q) {
+      double x = ss[q];
+      double t = S + x;
+      C += fabs(S) >= fabs(x) ? (S - t) + x : (x - t) + S;
+      S = t;
+      C += cc[q];
+    }
+    double* out = s == 0 ? A.out[0] : A.out[1];
+    if (out) out[p] = S + C;
+  }
 }
 
 // out[0] = Neumaier sum of e[0..n): one CTA of 256 threads, fixed order.
@@ -671,10 +709,27 @@ cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* 
   dim3 gp(64, ntrip);
   energy_prep<<<gp, 256, 0, st>>>(a, vtab, vt_stride, pv, pvt);
   dim3 grid(nchunks, ntrip);
-  if (a.kind == SAME)
-    energy_f32<false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
-  else
-    energy_f32<true><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+  if (a.kind == SAME) {
+    if (a.vmode)
+      energy_f32<false, true><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+    else
+      energy_f32<false, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+  } else {
+    if (a.vmode)
+      energy_f32<true, true><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+    else
+      energy_f32<true, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, bool MIXED, bool FM>
+cudaError_t launch_group(const EnergyArgs& a, const void* X, const void* Z, dim3 grid, size_t sm,
+                         cudaStream_t st) {
+  auto k = energy_group<T, MIXED, FM>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<grid, 256, sm, st>>>(a, (const T*)X, (const T*)Z);
   return cudaGetLastError();
 }
 
@@ -683,34 +738,29 @@ cudaError_t launch_energy(const EnergyArgs& a, const void* X, const void* Z, boo
   if (ntrip <= 0) return cudaSuccess;
   dim3 grid(nchunks, ntrip);
   const size_t sm = energy_smem_bytes(f64);
+  const bool mixed = a.kind != SAME, fm = a.vmode != 0;
   if (f64) {
-    if (a.kind == SAME) {
-      auto k = energy_group<double, false>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k<<<grid, 256, sm, st>>>(a, (const double*)X, (const double*)Z);
-    } else {
-      auto k = energy_group<double, true>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k<<<grid, 256, sm, st>>>(a, (const double*)X, (const double*)Z);
-    }
-  } else {
-    if (a.kind == SAME) {
-      auto k = energy_group<float, false>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k<<<grid, 256, sm, st>>>(a, (const float*)X, (const float*)Z);
-    } else {
-      auto k = energy_group<float, true>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k<<<grid, 256, sm, st>>>(a, (const float*)X, (const float*)Z);
-    }
+    if (!mixed) return fm ? launch_group<double, false, true>(a, X, Z, grid, sm, st)
+                          : launch_group<double, false, false>(a, X, Z, grid, sm, st);
+    return fm ? launch_group<double, true, true>(a, X, Z, grid, sm, st)
+              : launch_group<double, true, false>(a, X, Z, grid, sm, st);
   }
+  if (!mixed) return fm ? launch_group<float, false, true>(a, X, Z, grid, sm, st)
+                        : launch_group<float, false, false>(a, X, Z, grid, sm, st);
+  return fm ? launch_group<float, true, true>(a, X, Z, grid, sm, st)
+            : launch_group<float, true, false>(a, X, Z, grid, sm, st);
+}
+
+cudaError_t launch_reduce_partials(const double* partial, int np, const double* partial2,
+                                   int ntrip, double* e_trip, cudaStream_t st) {
+  if (ntrip <= 0) return cudaSuccess;
+  reduce_partials<<<ceil_div(ntrip, 128), 128, 0, st>>>(partial, np, partial2, ntrip, e_trip);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_partials(const double* partial, int np, int ntrip, double* e_trip,
-                                   cudaStream_t st) {
-  if (ntrip <= 0) return cudaSuccess;
-  reduce_partials<<<ceil_div(ntrip, 128), 128, 0, st>>>(partial, np, ntrip, e_trip);
+cudaError_t launch_orbital_partition(const OrbPartArgs& A, cudaStream_t st) {
+  if (A.na + A.nb <= 0) return cudaSuccess;
+  orbital_partition<<<A.na + A.nb, 256, 0, st>>>(A);
   return cudaGetLastError();
 }
 

@@ -35,8 +35,9 @@ cudaError_t launch_energy(const EnergyArgs& a, const void* X, const void* Z, boo
 cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* Z, float* vtab,
                               int64_t vt_stride, int pv, int pvt, int ntrip, int nchunks,
                               cudaStream_t st);
-cudaError_t launch_reduce_partials(const double* partial, int np, int ntrip, double* e_trip,
-                                   cudaStream_t st);
+cudaError_t launch_reduce_partials(const double* partial, int np, const double* partial2,
+                                   int ntrip, double* e_trip, cudaStream_t st);
+cudaError_t launch_orbital_partition(const OrbPartArgs& A, cudaStream_t st);
 cudaError_t launch_neumaier_sum(const double* e, int64_t n, double* out, cudaStream_t st);
 // pack.cu
 template <class St>
@@ -248,6 +249,7 @@ struct Run {
   int nbas, naux, no[2], nv[2];
   // DF factor blocks per spin (rows, K = naux)
   Operand Boo[2], Bov[2], Bvv[2];
+  const double* fov[2] = {nullptr, nullptr};  // f_ov blocks (both or none)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> contract_ev, energy_ev;
   lno_ot_stats* stats;
 
@@ -355,6 +357,19 @@ struct Run {
       sigB = pow2_scale(mb);
       sigT = pow2_scale(mt);
       stats->other_launches += 5;
+    }
+    if (dom->fov[0] || dom->fov[1]) {  // a missing spin block is zero
+      for (int s = 0; s < 2; ++s) {
+        if (dom->fov[s]) {
+          fov[s] = dom->fov[s];
+        } else {
+          double* z;
+          const size_t n = std::max<size_t>((size_t)no[s] * nv[s], 1);
+          TRY(arena.get(&z, n));
+          CU(cudaMemsetAsync(z, 0, n * sizeof(double), st));
+          fov[s] = z;
+        }
+      }
     }
     for (int s = 0; s < 2; ++s) {
       const int o = no[s], v = nv[s];
@@ -827,8 +842,9 @@ struct SpinPass {
                        R.st));
     const int target = R.ctx->nsm * 6;
     const int P = std::max(1, std::min((int)blocks.size(), target / G + 1));
+    const bool fov = R.fov[0] != nullptr;   // restricted open-shell f_ov term
     double* partial;
-    TRY(A.get(&partial, (size_t)G * P));
+    TRY(A.get(&partial, (size_t)G * P * (fov ? 2 : 1)));
     // float32 V tables of the tensor-core path, per triplet
     const int pv = (int)round_up(std::max(v, 1), 16), pvt = (int)round_up(std::max(vt, 1), 16);
     const int64_t vt_stride = is_mixed ? round_up(2LL * v * pvt + (int64_t)v * pv, 16)
@@ -971,7 +987,26 @@ struct SpinPass {
         CU(launch_energy_f32(ea, reinterpret_cast<const float*>(X),
                              reinterpret_cast<const float*>(Z), vtab, vt_stride, pv, pvt, ng, P,
                              R.st));
-      CU(launch_reduce_partials(partial, P, ng, eout + g0, R.st));
+      double* partial2 = nullptr;
+      if (fov) {
+        // the f_ov part of V in a second pass over the same X (and Z'):
+        // sum W V_f / D with V_f built like the T1 term from f_ov and T2
+        EnergyArgs ef = ea;
+        ef.vmode = 1;
+        ef.t1s = R.fov[s];
+        ef.t1t = R.fov[is_mixed ? t : s];
+        ef.t2ss = t2ss;
+        ef.t2st = t2st;
+        ef.partial = partial2 = partial + (size_t)G * P;
+        if (f64)
+          CU(launch_energy(ef, X, Z, f64, ng, P, R.st));
+        else
+          CU(launch_energy_f32(ef, reinterpret_cast<const float*>(X),
+                               reinterpret_cast<const float*>(Z), vtab, vt_stride, pv, pvt, ng,
+                               P, R.st));
+        R.stats->energy_launches += 2;
+      }
+      CU(launch_reduce_partials(partial, P, partial2, ng, eout + g0, R.st));
       if (e1) cudaEventRecord(e1, R.st);
       if (e0 && e1) R.energy_ev.push_back({e0, e1});
       R.stats->energy_launches += 2;
@@ -1010,7 +1045,6 @@ int validate(const lno_ot_ctx* ctx, const lno_ot_domain* d) {
   if (d->nbas <= 0 || d->naux <= 0) return LNO_OT_EINVAL;
   if (d->nocc[1] < 0 || d->nocc[1] > d->nocc[0] || d->nocc[0] > d->nbas) return LNO_OT_EINVAL;
   if ((int64_t)d->nbas * d->nbas * d->naux > ((int64_t)1 << 40)) return LNO_OT_EINVAL;
-  if (d->fov[0] || d->fov[1]) return LNO_OT_EUNSUPPORTED;
   for (int s = 0; s < 2; ++s) {
     TRY(check_ptr(ctx, d->B[s], true));
     TRY(check_ptr(ctx, d->eps[s], true));
@@ -1022,6 +1056,12 @@ int validate(const lno_ot_ctx* ctx, const lno_ot_domain* d) {
   TRY(check_ptr(ctx, d->t2bb, d->nocc[1] > 0 && vb));
   TRY(check_ptr(ctx, d->t2ab, d->nocc[0] > 0 && d->nocc[1] > 0 && va && vb));
   for (int c = 0; c < 4; ++c) TRY(check_ptr(ctx, d->e_trip[c], false));
+  for (int s = 0; s < 2; ++s) {
+    const bool has = d->nocc[s] > 0 && d->nocc[s] < d->nbas;
+    TRY(check_ptr(ctx, d->fov[s], false));
+    if (d->fov[s] && !has) return LNO_OT_EINVAL;   // nothing to hold
+    TRY(check_ptr(ctx, d->e_orb[s], false));
+  }
   return LNO_OT_OK;
 }
 
@@ -1078,6 +1118,26 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
         CU(cudaMemcpyAsync(dom->e_trip[c], e_int[c], cs[c].trips.size() * sizeof(double),
                            cudaMemcpyDeviceToDevice, R.st));
     }
+  }
+  // orbital contributions (eq cim_pt_energy) of the computed triplets
+  if (dom->e_orb[0] || dom->e_orb[1]) {
+    OrbPartArgs oa{};
+    oa.na = dom->nocc[0];
+    oa.nb = dom->nocc[1];
+    oa.out[0] = dom->e_orb[0];
+    oa.out[1] = dom->e_orb[1];
+    for (int c = 0; c < 4; ++c) {
+      oa.e[c] = e_int[c];
+      oa.n[c] = (int64_t)cs[c].trips.size();
+      Trip* dt;
+      TRY(R.arena.get(&dt, std::max<size_t>(cs[c].trips.size(), 1)));
+      if (!cs[c].trips.empty())
+        CU(cudaMemcpyAsync(dt, cs[c].trips.data(), cs[c].trips.size() * sizeof(Trip),
+                           cudaMemcpyHostToDevice, R.st));
+      oa.trips[c] = dt;
+    }
+    CU(launch_orbital_partition(oa, R.st));
+    R.stats->other_launches++;
   }
   double hs[4];
   CU(cudaMemcpyAsync(hs, ctx->d_sums, sizeof hs, cudaMemcpyDeviceToHost, R.st));
@@ -1430,6 +1490,7 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
 
 int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_grad* g) {
   TRY(validate(ctx, dom));
+  if (dom->fov[0] || dom->fov[1]) return LNO_OT_EUNSUPPORTED;  // adjoint of the f_ov term not built
   const int nbas = dom->nbas, naux = dom->naux;
   const int na = dom->nocc[0], nb = dom->nocc[1];
   const int va = nbas - na, vb = nbas - nb;

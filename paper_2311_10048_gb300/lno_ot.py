@@ -31,7 +31,8 @@ class Domain(C.Structure):
                 ("B", C.c_void_p * 2), ("eps", C.c_void_p * 2), ("t1", C.c_void_p * 2),
                 ("t2aa", C.c_void_p), ("t2bb", C.c_void_p), ("t2ab", C.c_void_p),
                 ("fov", C.c_void_p * 2), ("e_trip", C.c_void_p * 4),
-                ("trip_sel", C.c_void_p * 4), ("n_sel", C.c_int64 * 4)]
+                ("trip_sel", C.c_void_p * 4), ("n_sel", C.c_int64 * 4),
+                ("e_orb", C.c_void_p * 2)]
 
 
 class Result(C.Structure):
@@ -117,11 +118,14 @@ def _check_tensor(t, name):
         raise TypeError(f"{name} must be a contiguous float64 torch tensor")
 
 
-def make_domain_struct(dom, e_trip=None, trip_sel=None):
+def make_domain_struct(dom, e_trip=None, trip_sel=None, e_orb=None):
     """lno_ot_domain from a dict of device tensors (layouts as in the header).
 
-    ``e_trip``: optional list of 4 device float64 tensors (or None);
-    ``trip_sel``: optional list of 4 host int64 numpy arrays (or None).
+    ``dom["fov"]`` (optional): list of 2 device tensors (or None) with the
+    occupied-virtual Fock blocks; ``e_trip``: optional list of 4 device
+    float64 tensors (or None); ``trip_sel``: optional list of 4 host int64
+    numpy arrays (or None); ``e_orb``: optional list of 2 device float64
+    tensors [nocc[s]] for the orbital contributions.
     Returns (struct, keepalive) -- keep ``keepalive`` until the call returns.
     """
     d = Domain()
@@ -138,6 +142,13 @@ def make_domain_struct(dom, e_trip=None, trip_sel=None):
     d.t2aa, d.t2bb, d.t2ab = (dom["t2aa"].data_ptr(), dom["t2bb"].data_ptr(),
                               dom["t2ab"].data_ptr())
     keep = []
+    fov = dom.get("fov")
+    for s in (0, 1):
+        if fov is not None and fov[s] is not None:
+            _check_tensor(fov[s], f"fov[{s}]")
+            d.fov[s] = fov[s].data_ptr()
+        if e_orb is not None and e_orb[s] is not None:
+            d.e_orb[s] = e_orb[s].data_ptr()
     for c in range(4):
         if e_trip is not None and e_trip[c] is not None:
             d.e_trip[c] = e_trip[c].data_ptr()
@@ -182,9 +193,9 @@ class Context:
         except Exception:
             pass
 
-    def energy(self, dom, e_trip=None, trip_sel=None, raise_on_error=True):
+    def energy(self, dom, e_trip=None, trip_sel=None, raise_on_error=True, e_orb=None):
         """E(T) of one domain: dict aaa, aab, abb, bbb, total (floats)."""
-        d, keep = make_domain_struct(dom, e_trip, trip_sel)
+        d, keep = make_domain_struct(dom, e_trip, trip_sel, e_orb)
         r = Result()
         rc = self.lib.lno_ot_energy(self.h, C.byref(d), C.byref(r))
         del keep
@@ -242,11 +253,14 @@ def to_device(dom, device="cuda"):
 
     def t(x):
         return torch.as_tensor(x, dtype=torch.float64).contiguous().to(device)
-    return dict(nbas=int(dom["nbas"]), naux=int(dom["naux"]),
-                nocc=(int(dom["nocc"][0]), int(dom["nocc"][1])),
-                B=[t(dom["B"][0]), t(dom["B"][1])], eps=[t(dom["eps"][0]), t(dom["eps"][1])],
-                t1=[t(dom["t1"][0]), t(dom["t1"][1])], t2aa=t(dom["t2aa"]),
-                t2bb=t(dom["t2bb"]), t2ab=t(dom["t2ab"]))
+    out = dict(nbas=int(dom["nbas"]), naux=int(dom["naux"]),
+               nocc=(int(dom["nocc"][0]), int(dom["nocc"][1])),
+               B=[t(dom["B"][0]), t(dom["B"][1])], eps=[t(dom["eps"][0]), t(dom["eps"][1])],
+               t1=[t(dom["t1"][0]), t(dom["t1"][1])], t2aa=t(dom["t2aa"]),
+               t2bb=t(dom["t2bb"]), t2ab=t(dom["t2ab"]))
+    if dom.get("fov") is not None:
+        out["fov"] = [None if f is None else t(f) for f in dom["fov"]]
+    return out
 
 
 def _triples_autograd():

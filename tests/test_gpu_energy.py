@@ -151,9 +151,6 @@ def test_error_codes(ctx64, lib):
     s, keep = lno_ot.make_domain_struct(dd)
     s.eps[1] = host.data_ptr()
     assert ctx64.energy_raw(s)[0] == lno_ot.EDEVICE
-    s, keep = lno_ot.make_domain_struct(dd)
-    s.fov[0] = dd["eps"][0].data_ptr()
-    assert ctx64.energy_raw(s)[0] == lno_ot.EUNSUPPORTED
     s, keep = lno_ot.make_domain_struct(dd, trip_sel=[np.array([10 ** 6]), None, None, None])
     assert ctx64.energy_raw(s)[0] == lno_ot.EINVAL
     with pytest.raises(lno_ot.LnoError):
