@@ -107,8 +107,7 @@ typedef struct {
  *                 P(i/jk) P(a/bc) f_ia t^{bc}_{jk} to V (the T1 term with
  *                 f_ia for t^a_i and the doubles amplitude for <jk||bc>).
  *                 NULL for both spins = no such term; a NULL spin next to a
- *                 non-NULL one counts as zero.  lno_ot_backward returns
- *                 LNO_OT_EUNSUPPORTED when either is given.
+ *                 non-NULL one counts as zero.
  *   e_trip[c]     device float64 output, one value per computed triplet of
  *                 case c (0 aaa, 1 aab, 2 abb, 3 bbb): the triplet's
  *                 contribution sum_{restricted abc} W (W + V) / D.  NULL = not
@@ -151,7 +150,9 @@ typedef struct {
  * Gradients of inputs with symmetry are projected onto it: dB symmetric in
  * (p,q), dt2aa/dt2bb antisymmetric in (i,j) and in (a,b), so that
  * sum g * delta is the directional derivative for any symmetry-respecting
- * perturbation delta. */
+ * perturbation delta.  dfov[s] [nocc[s]][nvir[s]] is the gradient with
+ * respect to the f_ov block; it is defined (and returned) also when the
+ * domain has no f_ov block, as the derivative at f_ov = 0. */
 typedef struct {
   double* dB[2];
   double* deps[2];
@@ -159,6 +160,7 @@ typedef struct {
   double* dt2aa;
   double* dt2bb;
   double* dt2ab;
+  double* dfov[2];
 } lno_ot_grad;
 
 /* Timings and work counts of the last lno_ot_energy call on a context. */

@@ -91,7 +91,10 @@ __global__ void __launch_bounds__(256) gemm_f64_strided(const GemmS* __restrict_
 // Energy adjoint of one triplet group (float64 X).  Gradient outputs:
 //   dX (same layout as X, zeroed by the caller), dt1s/dt1t [n][nv],
 //   dov_ss (same layout as ovov_ss), dov_ts (as ovov_ts), deps_s/deps_t [nbas].
-template <bool MIXED>
+// FM (a.vmode 1, the f_ov part sum W V_f / D): dX is added to, dt1s/dt1t are
+// the f_ov gradients and dov_ss/dov_ts the raw T2 gradients (t2ss / t2st
+// layouts), since the planes are then the amplitudes themselves.
+template <bool MIXED, bool FM>
 __global__ void __launch_bounds__(256)
 energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __restrict__ Z,
                 double* __restrict__ dX, double* __restrict__ dZ, double* __restrict__ dt1s,
@@ -125,11 +128,7 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
         const int x = offs[pl][0] + r1, y = offs[pl][1] + r2;
         for (int o = 0; o < 3; ++o) {
           double v = 0.0;
-          if (x < nvs && y < nvs) {
-            const int p = occ3[o][0], r = occ3[o][1];
-            v = a.ovov_ss[ovss_idx(a, p, x, r, y)] -
-                a.ovov_ss[ovss_idx(a, p, y, r, x)];
-          }
+          if (x < nvs && y < nvs) v = vplane_ss(a, occ3[o][0], x, occ3[o][1], y);
           vt[pl * 3 + o][r1][r2] = v;
           gvt[pl * 3 + o][r1][r2] = 0.0;
         }
@@ -140,19 +139,14 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
         const int x = offs[pl] + r1, y = c0 + r2;
         for (int o = 0; o < 2; ++o) {
           double v = 0.0;
-          if (x < nvs && y < nvt) {
-            const int p = o == 0 ? tr.j : tr.i;
-            v = a.ovov_ts[ovts_idx(a, tr.k, y, p, x)];
-          }
+          if (x < nvs && y < nvt) v = vplane_ts(a, tr.k, y, o == 0 ? tr.j : tr.i, x);
           vt[pl * 2 + o][r1][r2] = v;
           gvt[pl * 2 + o][r1][r2] = 0.0;
         }
       }
       const int x = a0 + r1, y = b0 + r2;
       double v = 0.0;
-      if (x < nvs && y < nvs)
-        v = a.ovov_ss[ovss_idx(a, tr.i, x, tr.j, y)] -
-            a.ovov_ss[ovss_idx(a, tr.i, y, tr.j, x)];
+      if (x < nvs && y < nvs) v = vplane_ss(a, tr.i, x, tr.j, y);
       vt[4][r1][r2] = v;
       gvt[4][r1][r2] = 0.0;
     }
@@ -221,11 +215,16 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
                 t1s[6][cl] * vt[4][al][bl];
           }
           const double D = eocc - ev[0][al] - ev[1][bl] - ev[2][cl];
-          const double gw = gscale * (2.0 * w + v) / D;
+          // E = W (W + V) / D, or W V / D for the f_ov part
+          const double gw = gscale * (FM ? v : 2.0 * w + v) / D;
           const double gv = gscale * w / D;
-          const double gd = -gscale * w * (w + v) / (D * D);
+          const double gd = -gscale * w * (FM ? v : w + v) / (D * D);
           if (!MIXED) {
-            dXg[i1] = gw; dXg[i2] = -gw; dXg[i3] = gw;
+            if (FM) {
+              dXg[i1] += gw; dXg[i2] -= gw; dXg[i3] += gw;
+            } else {
+              dXg[i1] = gw; dXg[i2] = -gw; dXg[i3] = gw;
+            }
             for (int o = 0; o < 3; ++o) {
               gk_bc[o] += gv * t1s[o][al];
               atomicAdd(&gt1[o][al], gv * vt[o][bl][cl]);
@@ -235,7 +234,11 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
               atomicAdd(&gvt[6 + o][al][bl], gv * t1s[6 + o][cl]);
             }
           } else {
-            dXg[i1] = gw; dXg[i2] = -gw; dZg[i3] = gw;
+            if (FM) {
+              dXg[i1] += gw; dXg[i2] -= gw; dZg[i3] += gw;
+            } else {
+              dXg[i1] = gw; dXg[i2] = -gw; dZg[i3] = gw;
+            }
             gk_bc[0] += gv * t1s[0][al];             // (jb|KC)
             gk_bc[1] -= gv * t1s[1][al];             // (ib|KC)
             atomicAdd(&gt1[0][al], gv * vt[0][bl][cl]);
@@ -275,8 +278,12 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
           const double gk = gvt[pl * 3 + o][r1][r2];
           if (gk == 0.0) continue;
           const int p = occ3[o][0], r = occ3[o][1];
-          atomicAdd(&dov_ss[ovss_idx(a, p, x, r, y)], gk);
-          atomicAdd(&dov_ss[ovss_idx(a, p, y, r, x)], -gk);
+          if (FM) {
+            atomicAdd(&dov_ss[(((int64_t)p * nos + r) * nvs + x) * nvs + y], gk);
+          } else {
+            atomicAdd(&dov_ss[ovss_idx(a, p, x, r, y)], gk);
+            atomicAdd(&dov_ss[ovss_idx(a, p, y, r, x)], -gk);
+          }
         }
       }
     } else {
@@ -288,14 +295,21 @@ energy_backward(EnergyArgs a, const double* __restrict__ X, const double* __rest
           const double gk = gvt[pl * 2 + o][r1][r2];
           if (gk == 0.0) continue;
           const int p = o == 0 ? tr.j : tr.i;
-          atomicAdd(&dov_ts[ovts_idx(a, tr.k, y, p, x)], gk);
+          if (FM)
+            atomicAdd(&dov_ts[(((int64_t)p * a.not_ + tr.k) * nvs + x) * nvt + y], gk);
+          else
+            atomicAdd(&dov_ts[ovts_idx(a, tr.k, y, p, x)], gk);
         }
       }
       const int x = a0 + r1, y = b0 + r2;
       const double gk = gvt[4][r1][r2];
       if (x < nvs && y < nvs && gk != 0.0) {
-        atomicAdd(&dov_ss[ovss_idx(a, tr.i, x, tr.j, y)], gk);
-        atomicAdd(&dov_ss[ovss_idx(a, tr.i, y, tr.j, x)], -gk);
+        if (FM) {
+          atomicAdd(&dov_ss[(((int64_t)tr.i * nos + tr.j) * nvs + x) * nvs + y], gk);
+        } else {
+          atomicAdd(&dov_ss[ovss_idx(a, tr.i, x, tr.j, y)], gk);
+          atomicAdd(&dov_ss[ovss_idx(a, tr.i, y, tr.j, x)], -gk);
+        }
       }
     }
     if (tid < 3 * TB) {
@@ -608,12 +622,22 @@ cudaError_t launch_energy_backward(const EnergyArgs& a, const double* X, const d
                                    cudaStream_t st) {
   if (ntrip <= 0) return cudaSuccess;
   dim3 grid(nchunks, ntrip);
-  if (a.kind == SAME)
-    energy_backward<false><<<grid, 256, 0, st>>>(a, X, Z, dX, dZ, dt1s, dt1t, dov_ss, dov_ts,
-                                                 deps_s, deps_t, gscale);
-  else
-    energy_backward<true><<<grid, 256, 0, st>>>(a, X, Z, dX, dZ, dt1s, dt1t, dov_ss, dov_ts,
-                                                deps_s, deps_t, gscale);
+  const bool fm = a.vmode != 0;
+  if (a.kind == SAME) {
+    if (fm)
+      energy_backward<false, true><<<grid, 256, 0, st>>>(a, X, Z, dX, dZ, dt1s, dt1t, dov_ss,
+                                                         dov_ts, deps_s, deps_t, gscale);
+    else
+      energy_backward<false, false><<<grid, 256, 0, st>>>(a, X, Z, dX, dZ, dt1s, dt1t, dov_ss,
+                                                          dov_ts, deps_s, deps_t, gscale);
+  } else {
+    if (fm)
+      energy_backward<true, true><<<grid, 256, 0, st>>>(a, X, Z, dX, dZ, dt1s, dt1t, dov_ss,
+                                                        dov_ts, deps_s, deps_t, gscale);
+    else
+      energy_backward<true, false><<<grid, 256, 0, st>>>(a, X, Z, dX, dZ, dt1s, dt1t, dov_ss,
+                                                         dov_ts, deps_s, deps_t, gscale);
+  }
   return cudaGetLastError();
 }
 

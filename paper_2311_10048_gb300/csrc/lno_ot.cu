@@ -1177,6 +1177,7 @@ struct GradAcc {
   Operand dBoo[2], dBov[2], dBvv[2];  // same layout as the DF blocks
   double* dt1[2];
   double* deps[2];
+  double* dfov[2];                    // f_ov gradients (when the domain has f_ov)
   double* dt2aa;
   double* dt2bb;
   double* dt2ab;
@@ -1356,6 +1357,17 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
       ea.trips = dtrips + g0;
       CU(launch_energy_backward(ea, X, Z, dX, dZ, G.dt1[s], G.dt1[is_mixed ? t : s], dovss,
                                 dovts, G.deps[s], G.deps[is_mixed ? t : s], gE, ng, Pch, st));
+      if (R.fov[0]) {  // the f_ov part: planes are T2 amplitudes, coefficients f_ov
+        EnergyArgs ef = ea;
+        ef.vmode = 1;
+        ef.t1s = R.fov[s];
+        ef.t1t = R.fov[is_mixed ? t : s];
+        ef.t2ss = P.t2ss;
+        ef.t2st = P.t2st;
+        CU(launch_energy_backward(ef, X, Z, dX, dZ, G.dfov[s], G.dfov[is_mixed ? t : s], dt2ss,
+                                  dt2st, G.deps[s], G.deps[is_mixed ? t : s], gE, ng, Pch, st));
+        R.stats->energy_launches += 1;
+      }
       // contraction adjoint: dA += sign dX.B, dB += sign dX^T.A
       auto adj = [&](const std::vector<std::vector<SegRef>>& segs, const double* dXb, int64_t Nn,
                      int Mm, int ldo) -> int {
@@ -1490,7 +1502,6 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
 
 int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_grad* g) {
   TRY(validate(ctx, dom));
-  if (dom->fov[0] || dom->fov[1]) return LNO_OT_EUNSUPPORTED;  // adjoint of the f_ov term not built
   const int nbas = dom->nbas, naux = dom->naux;
   const int na = dom->nocc[0], nb = dom->nocc[1];
   const int va = nbas - na, vb = nbas - nb;
@@ -1502,6 +1513,7 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
     TRY(check_ptr(ctx, g->dB[s], false));
     TRY(check_ptr(ctx, g->deps[s], false));
     TRY(check_ptr(ctx, g->dt1[s], false));
+    TRY(check_ptr(ctx, g->dfov[s], false));
   }
   TRY(check_ptr(ctx, g->dt2aa, false));
   TRY(check_ptr(ctx, g->dt2bb, false));
@@ -1516,6 +1528,14 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
   CaseSel cs[4];
   for (int c = 0; c < 4; ++c) TRY(select_case(dom, c, cs[c]));
   TRY(R.stage());
+  if (!R.fov[0] && (g->dfov[0] || g->dfov[1])) {
+    // dE/df_ov at f_ov = 0 (E is affine in f_ov): run the f_ov pass on zeros
+    for (int s = 0; s < 2; ++s) {
+      double* z;
+      TRY(zeros(R.arena, &z, n1[s], R.st));
+      R.fov[s] = z;
+    }
+  }
   Arena GA(R.st, 0);
   GradAcc G{};
   for (int s = 0; s < 2; ++s) {
@@ -1523,6 +1543,8 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
     TRY(zero_operand_like(GA, R.Bov[s], G.dBov[s], R.st));
     TRY(zero_operand_like(GA, R.Bvv[s], G.dBvv[s], R.st));
     TRY(zeros(GA, &G.dt1[s], n1[s], R.st));
+    G.dfov[s] = nullptr;
+    if (R.fov[0]) TRY(zeros(GA, &G.dfov[s], n1[s], R.st));
     TRY(zeros(GA, &G.deps[s], nbas, R.st));
   }
   // T2 gradients accumulate in the caller's buffers when given (projected in
@@ -1565,6 +1587,7 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
     }
     if (g->deps[s]) CU(launch_scale_copy(G.deps[s], nbas, 1.0, g->deps[s], R.st));
     if (g->dt1[s]) CU(launch_scale_copy(G.dt1[s], n1[s], 1.0, g->dt1[s], R.st));
+    if (g->dfov[s]) CU(launch_scale_copy(G.dfov[s], n1[s], 1.0, g->dfov[s], R.st));
   }
   if (g->dt2aa) CU(launch_antisym_inplace(g->dt2aa, na, va, R.st));
   if (g->dt2bb) CU(launch_antisym_inplace(g->dt2bb, nb, vb, R.st));

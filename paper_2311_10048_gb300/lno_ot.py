@@ -41,7 +41,8 @@ class Result(C.Structure):
 
 class Grad(C.Structure):
     _fields_ = [("dB", C.c_void_p * 2), ("deps", C.c_void_p * 2), ("dt1", C.c_void_p * 2),
-                ("dt2aa", C.c_void_p), ("dt2bb", C.c_void_p), ("dt2ab", C.c_void_p)]
+                ("dt2aa", C.c_void_p), ("dt2bb", C.c_void_p), ("dt2ab", C.c_void_p),
+                ("dfov", C.c_void_p * 2)]
 
 
 class Stats(C.Structure):
@@ -229,7 +230,7 @@ class Context:
         d, keep = make_domain_struct(dom, trip_sel=trip_sel)
         g = Grad()
         for s in (0, 1):
-            for key in ("dB", "deps", "dt1"):
+            for key in ("dB", "deps", "dt1", "dfov"):
                 if grads.get(key) is not None and grads[key][s] is not None:
                     getattr(g, key)[s] = grads[key][s].data_ptr()
         for key in ("dt2aa", "dt2bb", "dt2ab"):
@@ -271,33 +272,42 @@ def _triples_autograd():
 
         Forward calls lno_ot_energy (the context's precision); backward calls
         lno_ot_backward (float64 adjoint, W recomputed per triplet).  Inputs
-        are the device tensors of the domain; gradients of B and of the
-        same-spin T2 blocks are projected onto their symmetry.
+        are the device tensors of the domain (the two f_ov blocks may be
+        None); gradients of B and of the same-spin T2 blocks are projected
+        onto their symmetry.
         """
 
         @staticmethod
-        def forward(fctx, Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab, meta):
-            handle, nocc, naux, trip_sel = meta
+        def _dom(meta, Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab, fa, fb):
+            _, nocc, naux, _ = meta
             dom = dict(nbas=Ba.shape[1], naux=naux, nocc=nocc, B=[Ba, Bb], eps=[ea, eb],
                        t1=[t1a, t1b], t2aa=t2aa, t2bb=t2bb, t2ab=t2ab)
+            if fa is not None or fb is not None:
+                dom["fov"] = [fa, fb]
+            return dom
+
+        @staticmethod
+        def forward(fctx, Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab, fa, fb, meta):
+            handle, trip_sel = meta[0], meta[3]
+            dom = LnoTriples._dom(meta, Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab, fa, fb)
             out = handle.energy(dom, trip_sel=trip_sel)
-            fctx.save_for_backward(Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab)
+            fctx.save_for_backward(Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab, fa, fb)
             fctx.meta = meta
             return torch.tensor(out["total"], dtype=torch.float64, device=Ba.device)
 
         @staticmethod
         def backward(fctx, gE):
-            Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab = fctx.saved_tensors
-            handle, nocc, naux, trip_sel = fctx.meta
-            dom = dict(nbas=Ba.shape[1], naux=naux, nocc=nocc, B=[Ba, Bb], eps=[ea, eb],
-                       t1=[t1a, t1b], t2aa=t2aa, t2bb=t2bb, t2ab=t2ab)
+            Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab, fa, fb = fctx.saved_tensors
+            handle, trip_sel = fctx.meta[0], fctx.meta[3]
+            dom = LnoTriples._dom(fctx.meta, Ba, Bb, ea, eb, t1a, t1b, t2aa, t2bb, t2ab, fa, fb)
             need = fctx.needs_input_grad
-            z = lambda x, k: torch.empty_like(x) if need[k] else None
+            z = lambda x, k: torch.empty_like(x) if need[k] and x is not None else None
             g = dict(dB=[z(Ba, 0), z(Bb, 1)], deps=[z(ea, 2), z(eb, 3)], dt1=[z(t1a, 4), z(t1b, 5)],
-                     dt2aa=z(t2aa, 6), dt2bb=z(t2bb, 7), dt2ab=z(t2ab, 8))
+                     dt2aa=z(t2aa, 6), dt2bb=z(t2bb, 7), dt2ab=z(t2ab, 8),
+                     dfov=[z(fa, 9), z(fb, 10)])
             handle.backward(dom, float(gE), g, trip_sel=trip_sel)
             return (g["dB"][0], g["dB"][1], g["deps"][0], g["deps"][1], g["dt1"][0], g["dt1"][1],
-                    g["dt2aa"], g["dt2bb"], g["dt2ab"], None)
+                    g["dt2aa"], g["dt2bb"], g["dt2ab"], g["dfov"][0], g["dfov"][1], None)
 
     return LnoTriples
 
@@ -310,6 +320,7 @@ def triples_energy(ctx, dom, trip_sel=None):
     global _LNO_FN
     if _LNO_FN is None:
         _LNO_FN = _triples_autograd()
+    fov = dom.get("fov") or [None, None]
     return _LNO_FN.apply(dom["B"][0], dom["B"][1], dom["eps"][0], dom["eps"][1], dom["t1"][0],
-                         dom["t1"][1], dom["t2aa"], dom["t2bb"], dom["t2ab"],
+                         dom["t1"][1], dom["t2aa"], dom["t2bb"], dom["t2ab"], fov[0], fov[1],
                          (ctx, tuple(dom["nocc"]), int(dom["naux"]), trip_sel))

@@ -47,10 +47,10 @@ def test_ctypes_struct_layouts_match_c(tmp_path):
         int main(void) {
           printf("%zu %zu %zu %zu %zu\\n", sizeof(lno_ot_options), sizeof(lno_ot_domain),
                  sizeof(lno_ot_result), sizeof(lno_ot_grad), sizeof(lno_ot_stats));
-          printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(lno_ot_domain, t2ab),
+          printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(lno_ot_domain, t2ab),
                  offsetof(lno_ot_domain, e_trip), offsetof(lno_ot_domain, n_sel),
                  offsetof(lno_ot_stats, elements), offsetof(lno_ot_domain, fov),
-                 offsetof(lno_ot_domain, e_orb));
+                 offsetof(lno_ot_domain, e_orb), offsetof(lno_ot_grad, dfov));
           return 0;
         }
     """))
@@ -63,7 +63,8 @@ def test_ctypes_struct_layouts_match_c(tmp_path):
     want = [C.sizeof(lno_ot.Options), C.sizeof(lno_ot.Domain), C.sizeof(lno_ot.Result),
             C.sizeof(lno_ot.Grad), C.sizeof(lno_ot.Stats),
             lno_ot.Domain.t2ab.offset, lno_ot.Domain.e_trip.offset, lno_ot.Domain.n_sel.offset,
-            lno_ot.Stats.elements.offset, lno_ot.Domain.fov.offset, lno_ot.Domain.e_orb.offset]
+            lno_ot.Stats.elements.offset, lno_ot.Domain.fov.offset, lno_ot.Domain.e_orb.offset,
+            lno_ot.Grad.dfov.offset]
     assert got == want
 
 

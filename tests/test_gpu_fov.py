@@ -178,15 +178,6 @@ def test_batched_with_fov_equals_single(lib):
             assert r[c] == s1[c]
 
 
-def test_backward_with_fov_is_unsupported(ctx64):
-    d, _ = c0f()
-    dd = lno_ot.to_device(d)
-    g = dict(deps=[torch.empty_like(dd["eps"][0]), torch.empty_like(dd["eps"][1])])
-    with pytest.raises(lno_ot.LnoError) as e:
-        ctx64.backward(dd, 1.0, g)
-    assert e.value.code == lno_ot.EUNSUPPORTED
-
-
 def test_fov_on_spin_without_virtuals_is_rejected(ctx64):
     d = make_domain(5, (5, 3), naux=10, L=4.0, seed=11)    # spin up: no virtual
     dd = lno_ot.to_device(d)

@@ -142,3 +142,78 @@ def test_c4_subset_gradient_vs_oracle(ctx64):
     g, e = gpu_grad(ctx64, d, sel)
     assert abs(e - e_ref) <= 1e-10 * abs(e_ref)
     compare(g, g_ref)
+
+
+# ---- with the restricted open-shell f_ov block -------------------------------
+from paper_2311_10048_gb300.synth import add_fov  # noqa: E402
+
+KEYS_F = KEYS + ["f0", "f1"]
+
+
+def oracle_grad_fov(d):
+    dt = T.as_tensors(d, requires_grad=True)
+    E = T.energy_graph(dt)
+    E.backward()
+    grads, _ = [], None
+    ins = [dt["B"][0], dt["B"][1], dt["eps"][0], dt["eps"][1], dt["t1"][0], dt["t1"][1],
+           dt["t2aa"], dt["t2bb"], dt["t2ab"], dt["fov"][0], dt["fov"][1]]
+    for x in ins:
+        grads.append(torch.zeros_like(x) if x.grad is None else x.grad)
+    sym = lambda g: 0.5 * (g + g.transpose(1, 2))
+    asym = lambda g: 0.25 * (g - g.transpose(0, 1) - g.transpose(2, 3) + g.transpose(0, 1).transpose(2, 3))
+    grads[0], grads[1] = sym(grads[0]), sym(grads[1])
+    grads[6], grads[7] = asym(grads[6]), asym(grads[7])
+    return grads, float(E.detach())
+
+
+def gpu_grad_fov(ctx, d, fov_given=True):
+    dd = lno_ot.to_device(d)
+    if not fov_given:
+        dd["fov"] = [torch.zeros_like(dd["t1"][0]), torch.zeros_like(dd["t1"][1])]
+    ins = [dd["B"][0], dd["B"][1], dd["eps"][0], dd["eps"][1], dd["t1"][0], dd["t1"][1],
+           dd["t2aa"], dd["t2bb"], dd["t2ab"], dd["fov"][0], dd["fov"][1]]
+    for x in ins:
+        x.requires_grad_(True)
+    dom = dict(dd, B=ins[0:2], eps=ins[2:4], t1=ins[4:6], t2aa=ins[6], t2bb=ins[7],
+               t2ab=ins[8], fov=ins[9:11])
+    E = lno_ot.triples_energy(ctx, dom)
+    return [g.detach().cpu() for g in torch.autograd.grad(E, ins)], float(E.detach())
+
+
+@pytest.mark.parametrize("shape", [(9, 3, 2, 1), (12, 4, 4, 2), (10, 4, 1, 3), (20, 5, 3, 4)])
+def test_gradient_with_fov_matches_oracle(ctx64, shape):
+    nbas, na, nb, seed = shape
+    d = add_fov(make_domain(nbas, (na, nb), naux=2 * nbas, L=nbas / 2, seed=seed, t1_sd=0.05),
+                sd=0.05, seed=seed)
+    g_ref, e_ref = oracle_grad_fov(d)
+    g, e = gpu_grad_fov(ctx64, d)
+    assert abs(e - e_ref) <= 1e-12 * max(1.0, abs(e_ref))
+    for k, a, b in zip(KEYS_F, g, g_ref):
+        scale = float(b.abs().max()) if b.numel() else 0.0
+        if scale == 0.0:
+            assert float(a.abs().max()) <= 1e-14, k
+            continue
+        assert float((a - b).abs().max()) <= 1e-6 * scale, (k, float((a - b).abs().max()), scale)
+
+
+def test_fov_gradient_at_zero_block(ctx64, lib):
+    # dE/df_ov at f_ov = 0, requested from a domain without an f_ov block,
+    # equals the gradient of a domain whose block is explicitly zero
+    d = make_domain(12, (4, 3), naux=24, L=6.0, seed=5, t1_sd=0.05)
+    dd = lno_ot.to_device(d)
+    gA = dict(dfov=[torch.empty_like(dd["t1"][0]), torch.empty_like(dd["t1"][1])])
+    ctx64.backward(dd, 1.0, gA)
+    gz, _ = gpu_grad_fov(ctx64, d, fov_given=False)
+    for s in (0, 1):
+        ref = gz[9 + s]
+        assert float(ref.abs().max()) > 0
+        assert float((gA["dfov"][s].cpu() - ref).abs().max()) <= 1e-12 * float(ref.abs().max())
+    # and central differences along a random f_ov direction
+    rng = np.random.default_rng(3)
+    x = [rng.standard_normal(dd["t1"][s].shape) for s in (0, 1)]
+    h = 1e-5
+    E = lambda sg: ctx64.energy(dict(dd, fov=[sg * h * torch.as_tensor(x[s], device="cuda")
+                                              for s in (0, 1)]))["total"]
+    fd = (E(+1) - E(-1)) / (2 * h)
+    an = sum(float((gA["dfov"][s].cpu() * torch.as_tensor(x[s])).sum()) for s in (0, 1))
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (fd, an)
