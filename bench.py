@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from paper_2311_10048_gb300.synth import (CONFIGS, c3_shapes, domain_bytes,  # noqa: E402
-                                          make_domain)
+from paper_2311_10048_gb300.synth import (CONFIGS, add_fov, c3_shapes,  # noqa: E402
+                                          domain_bytes, make_domain)
 
 METRIC = "open-shell E(T) TFLOP/s & domains/s at |dE(T)|<=1e-7 Eh vs plain FP64 GPU path"
 UNIT = "TFLOP/s"
@@ -46,6 +46,29 @@ def peaks():
     d = dict(PEAKS_FALLBACK)
     d["source"] = "fallback"
     return d
+
+
+# DRAM bytes (read + write) per tensor-core flop of the BF16X6 contraction,
+# from one ncu capture of that kernel on a c1-sized group (nbas 368, nocc
+# 8/6, naux 1200: 8.626 GB over 9 217 296 MMAs of 128x128x16); the per-launch
+# traffic scales with the launch's tensor flops at a fixed virtual space.
+DRAM_BYTES_PER_TENSOR_FLOP_X6 = 8.626e9 / (9217296 * 128 * 128 * 16 * 2)
+
+# FP32 operations per restricted (abc) element in the float32 energy kernel
+# (an FMA counts 2): W 2, V 17 (same spin) / 9 (mixed), W (W + V) 2,
+# double-float denominator 9, reciprocal + Newton step + product 6, sum 1.
+ENERGY_FLOPS_PER_ELEMENT = {"same": 37, "mixed": 29}
+
+
+def energy_elements(nocc, nbas):
+    """Restricted (abc) elements of the same-spin and mixed cases."""
+    na, nb = nocc
+    va, vb = nbas - na, nbas - nb
+    c2 = lambda n: n * (n - 1) // 2
+    c3 = lambda n: n * (n - 1) * (n - 2) // 6
+    same = c3(na) * c3(va) + c3(nb) * c3(vb)
+    mixed = c2(na) * nb * c2(va) * vb + c2(nb) * na * c2(vb) * va
+    return same, mixed
 
 
 def alg_flops_triplet(case, nocc, nbas):
@@ -363,6 +386,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--fp64-sample", type=int, default=2, help="FP64-path triplets per case")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fov", action="store_true",
+                    help="restricted open-shell domain: add an f_ov block (and time the "
+                         "orbital contributions too)")
     ap.add_argument("--shape", default=None,
                     help="custom domain nbas,nalpha,nbeta,naux (recipe of the configs, seed 5)")
     args = ap.parse_args()
@@ -395,6 +421,8 @@ def main():
     cfg["seed"] = cfg["seed"] + 1000 * rank
     t_gen = time.time()
     dom = make_domain(**cfg)
+    if args.fov:
+        dom = add_fov(dom, sd=0.02, seed=cfg["seed"])
     t_gen = time.time() - t_gen
     nbas, nocc = dom["nbas"], dom["nocc"]
     sel = sample_triplets(nocc, args.cpu_sample)
@@ -416,8 +444,10 @@ def main():
 
     # warm-up (the last one also returns per-triplet contributions for parity)
     et = [torch.zeros(max(ntrip(c, nocc), 1), dtype=torch.float64, device=dev) for c in CASES]
+    eorb = ([torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in nocc]
+            if args.fov else None)
     for w in range(args.warmup):
-        out = ctx.energy(dd, e_trip=et if w == args.warmup - 1 else None)
+        out = ctx.energy(dd, e_trip=et if w == args.warmup - 1 else None, e_orb=eorb)
     torch.cuda.synchronize()
     parity = None
     if oracle_vals is not None:
@@ -439,7 +469,7 @@ def main():
     with ClockSampler(local) as clk:
         e0.record(st)
         for _ in range(args.steps):
-            out = ctx.energy(dd)
+            out = ctx.energy(dd, e_orb=eorb)
             stats.append(ctx.stats())
         e1.record(st)
         torch.cuda.synchronize()
@@ -455,7 +485,8 @@ def main():
     clocks = clk.summary()
 
     # end to end: host (pinned) inputs -> device -> E(T) -> host, per step
-    host = {k: dom[k] for k in ("B", "eps", "t1", "t2aa", "t2bb", "t2ab")}
+    host = {k: dom[k] for k in ("B", "eps", "t1", "t2aa", "t2bb", "t2ab")
+            + (("fov",) if args.fov else ())}
     pinned = {}
     h2d = 0
     for k, v in host.items():
@@ -474,7 +505,7 @@ def main():
             dn[k] = ([x.to(dev, non_blocking=True) for x in v] if isinstance(v, list)
                      else v.to(dev, non_blocking=True))
         torch.cuda.synchronize()
-        out_e2e = ctx.energy(dn)          # returns after the result is on the host
+        out_e2e = ctx.energy(dn, e_orb=eorb)   # returns after the result is on the host
         del dn
     e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
     ctx.close()
@@ -503,6 +534,17 @@ def main():
     peak = pk.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
     launches = sum(s["contract_launches"] + s["energy_launches"] + s["other_launches"]
                    for s in stats)
+    traffic = (DRAM_BYTES_PER_TENSOR_FLOP_X6 * tc_flops_launch / 1e9
+               if args.precision == "bf16x6" else None)
+    # the float32 energy kernel is bound by the FP32 ALUs: peak = 152 SMs x 128
+    # FP32 lanes x 2 flop (FMA) x the SM clock seen under load
+    n_same, n_mixed = energy_elements(nocc, nbas)
+    passes = 2 if args.fov else 1
+    en_flops = passes * (n_same * ENERGY_FLOPS_PER_ELEMENT["same"]
+                         + n_mixed * ENERGY_FLOPS_PER_ELEMENT["mixed"])
+    mhz = clocks.get("sm_mhz") or 2070.0
+    en_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    en_achieved = en_flops / (s_last["ms_energy"] / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -511,7 +553,8 @@ def main():
         "precision": (f"{args.precision.upper()}: exact BF16 slices of float64 operands on "
                       f"tcgen05 (FP32 TMEM accumulators per weight class), float64 "
                       f"denominators and compensated sums"),
-        "config": {"workload": workload_name(args.config), **cfg_public(cfg),
+        "config": {"workload": workload_name(args.config) + (" + f_ov (RO reference)" if args.fov else ""),
+                   **cfg_public(cfg), **({"fov_sd": 0.02} if args.fov else {}),
                    "l2": f"inputs larger than L2 ({domain_bytes(nbas, nocc, dom['naux']) / 1e9:.1f} GB)",
                    "parallelism": f"replicas x{world} (one domain per GPU)"},
         "domains_per_s": world * args.steps / (ms_max / 1e3),
@@ -519,9 +562,16 @@ def main():
         "parity": parity,
         "roofline": {"kernel": "tc_gemm_sliced (W contraction)", "bound": "tensor",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_unit": "GB per launch (ncu DRAM bytes per tensor flop, scaled)",
                      "peak_source": f"{pk['source']} bf16 sustained",
                      "per_launch": {"ms": tc_launch_ms, "tensor_flops": tc_flops_launch}},
+        "roofline_energy": {"kernel": "energy_f32 (W/V assembly, W(W+V)/D, sums)",
+                            "bound": "alu", "achieved": en_achieved, "peak": en_peak,
+                            "unit": "TFLOP/s (FP32)", "frac": en_achieved / en_peak,
+                            "elements": n_same + n_mixed, "passes": passes,
+                            "elements_per_s": passes * (n_same + n_mixed) / (s_last["ms_energy"] / 1e3),
+                            "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock"},
         "breakdown_ms": {k: s_last[k] for k in ("ms_total", "ms_stage", "ms_contract",
                                                 "ms_energy")},
         "gpu_launches": int(launches),

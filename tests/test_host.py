@@ -92,3 +92,12 @@ def test_two_rank_gloo_sharding_round_trip():
     for _, _, merged, t in res:
         assert merged == {i: float(i + 1) ** 2 for i in range(20)}
         assert t == 11.0
+
+
+def test_energy_element_counts_match_published_totals():
+    import bench
+    want = {"c0": 2.1e6, "c1": 1.50e12, "c2": 6.45e13, "c4": 2.1e10}
+    for name, ref in want.items():
+        c = CONFIGS[name]
+        same, mixed = bench.energy_elements(c["nocc"], c["nbas"])
+        assert abs(same + mixed - ref) / ref < 0.03, (name, same + mixed, ref)
