@@ -542,6 +542,44 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
       if ((rowok[0] || rowok[1]) && aend > al0) {
         const float* x1r0 = T1 + ((bl0 + 0) * TB + cl) * P1;
         const float* x1r1 = T1 + ((bl0 + 1) * TB + cl) * P1;
+        if constexpr (MIXED) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          // mixed spin: all 8 x 2 elements are evaluated and masked with a
+          // select (a < b also bounds a by aend), so the independent element
+          // chains interleave; the same-spin tiles keep the branches (more of
+          // their elements are masked on the diagonal blocks)
+          const int a4 = al0 + 4 * h;
+          const float4 q0 = *reinterpret_cast<const float4*>(x1r0 + a4);
+          const float4 q1 = *reinterpret_cast<const float4*>(x1r1 + a4);
+          const float x1a[2][4] = {{q0.x, q0.y, q0.z, q0.w}, {q1.x, q1.y, q1.z, q1.w}};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int al = a4 + u;
+            const float4 da = ad[al];
+            const float del = ael[al];
+            const float2 x2 = *reinterpret_cast<const float2*>(T2 + (al * TB + cl) * P2 + bl0);
+            const float4 vac = kac[al][cl];
+            const float x2a[2] = {x2.x, x2.y};
+#pragma unroll
+            for (int sb = 0; sb < 2; ++sb) {
+              const int bl = bl0 + sb;
+              const bool valid = rowok[sb] && a0 + al < b0 + bl;
+              const float x3 = T3[(al * TB + bl) * P3 + cl];
+              const float vab = kab[al][bl].x;
+              const float w = x1a[sb][u] - x2a[sb] + x3;
+              const float v = da.x * k0[sb] - da.y * k1[sb] - tb0[sb] * vac.x +
+                              tb1[sb] * vac.y + tc0 * vab;
+              const float num = FM ? __fmul_rn(w, v) : __fmul_rn(w, __fadd_rn(w, v));
+              float s, e;
+              two_sum(dbc[sb].hi, -da.w, s, e);
+              const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc[sb].lo, del)));
+              const float qv = div_nr(num, D);
+              part = __fadd_rn(part, valid ? qv : 0.f);
+            }
+          }
+        }
+        } else {
         for (int a4 = al0; a4 < aend; a4 += 4) {
           const float4 q0 = *reinterpret_cast<const float4*>(x1r0 + a4);
           const float4 q1 = *reinterpret_cast<const float4*>(x1r1 + a4);
@@ -581,6 +619,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
               }
             }
           }
+        }
         }
         float s, e;
         two_sum(acc.hi, part, s, e);
