@@ -99,6 +99,15 @@ typedef struct {
  *   t2ab    [na][nb][nva][nvb]   t2ab[i][J][a][B] = t^{aB}_{iJ}
  * High spin: 0 <= nocc[1] <= nocc[0] <= nbas.
  *
+ * Closed-shell domains (no singly occupied orbital): when both spins are given
+ * by the same arrays (B[0] == B[1], eps[0] == eps[1], t1[0] == t1[1],
+ * t2aa == t2bb, fov[0] == fov[1] as pointers, nocc[0] == nocc[1]), no
+ * trip_sel is set, and t2ab[i][J][a][B] equals t2ab[J][i][B][a] to within
+ * 1e-12 of the largest |t2ab| for every element (checked on the device), E_bbb
+ * and E_abb are the spin-flip images of E_aaa and E_aab, triplet for triplet;
+ * only the spin-up cases are computed and the others are copies.  Otherwise
+ * all four cases run.
+ *
  * Optional:
  *   fov[s]        [nocc[s]][nvir[s]] f_ia: the occupied-virtual block of the
  *                 Fock matrix in the semicanonical basis, non-zero for a

@@ -63,6 +63,8 @@ cudaError_t launch_pack_at2(const int2*, int, int, int, int, int, int, const dou
                             const double*, St, cudaStream_t);
 cudaError_t launch_transpose_t2ab(const double*, int, int, int, int, double*, cudaStream_t);
 cudaError_t launch_absmax(const double*, int64_t, unsigned long long*, cudaStream_t);
+cudaError_t launch_t2ab_flip_mismatch(const double* t2ab, int n, int v, double tol,
+                                     unsigned int* count, cudaStream_t s);
 cudaError_t launch_gather_rows(const void* src, void* dst, const int* list, int nlist,
                                int64_t row_bytes, int nslice, int64_t src_slice_bytes,
                                int64_t dst_slice_bytes, cudaStream_t s);
@@ -1083,18 +1085,46 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
   double* e_int[4];
   for (int c = 0; c < 4; ++c)
     TRY(R.arena.get(&e_int[c], std::max<size_t>(cs[c].trips.size(), 1)));
+  // Closed-shell domain (both spins given by the same arrays, spin-flip
+  // symmetric mixed amplitudes): bbb and abb are the spin-flip images of aaa
+  // and aab, with identical values, so only the spin-up pass runs.
+  bool flip = dom->nocc[0] == dom->nocc[1] && dom->B[0] == dom->B[1] &&
+              dom->eps[0] == dom->eps[1] && dom->t1[0] == dom->t1[1] &&
+              dom->t2aa == dom->t2bb && dom->fov[0] == dom->fov[1];
+  for (int c = 0; c < 4; ++c) flip = flip && dom->trip_sel[c] == nullptr;
+  if (flip && dom->nocc[0] > 0 && dom->nocc[0] < dom->nbas) {
+    // symmetric to within 1e-12 of the largest amplitude: amplitudes from a
+    // closed-shell calculation agree with their spin-flip images to rounding
+    const int n = dom->nocc[0], v = dom->nbas - dom->nocc[0];
+    CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), R.st));
+    CU(launch_absmax(dom->t2ab, (int64_t)n * n * v * v, ctx->d_amax, R.st));
+    unsigned long long hm = 0;
+    CU(cudaMemcpyAsync(&hm, ctx->d_amax, sizeof hm, cudaMemcpyDeviceToHost, R.st));
+    CU(cudaStreamSynchronize(R.st));
+    double amax;
+    std::memcpy(&amax, &hm, 8);
+    unsigned int* cnt;
+    TRY(R.arena.get(&cnt, 1));
+    CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), R.st));
+    CU(launch_t2ab_flip_mismatch(dom->t2ab, n, v, 1e-12 * amax, cnt, R.st));
+    unsigned int h = 1;
+    CU(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, R.st));
+    CU(cudaStreamSynchronize(R.st));
+    R.stats->other_launches += 2;
+    flip = h == 0;
+  }
   TRY(R.stage());
   {
     SpinPass pa(R, 0, cs[0], cs[1], e_int[0], e_int[1]);
     SpinPass pb(R, 1, cs[3], cs[2], e_int[3], e_int[2]);
     if (!R.f64) {  // integral scale: first pass over every DF block both spins need
       pa.plan();
-      pb.plan();
+      if (!flip) pb.plan();
       TRY(pa.prepare_inputs());
-      TRY(pb.prepare_inputs());
+      if (!flip) TRY(pb.prepare_inputs());
       CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), R.st));
       TRY(pa.measure());
-      TRY(pb.measure());
+      if (!flip) TRY(pb.measure());
       unsigned long long h;
       CU(cudaMemcpyAsync(&h, ctx->d_amax, sizeof h, cudaMemcpyDeviceToHost, R.st));
       CU(cudaStreamSynchronize(R.st));
@@ -1105,7 +1135,16 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
     if (t1) cudaEventRecord(t1, R.st);
     TRY(pa.run());
     pa.own.release();
-    TRY(pb.run());
+    if (!flip) {
+      TRY(pb.run());
+    } else {  // spin-flip images: bbb = aaa, abb = aab, triplet for triplet
+      if (!cs[3].trips.empty())
+        CU(cudaMemcpyAsync(e_int[3], e_int[0], cs[3].trips.size() * sizeof(double),
+                           cudaMemcpyDeviceToDevice, R.st));
+      if (!cs[2].trips.empty())
+        CU(cudaMemcpyAsync(e_int[2], e_int[1], cs[2].trips.size() * sizeof(double),
+                           cudaMemcpyDeviceToDevice, R.st));
+    }
   }
   // per-case sums
   for (int c = 0; c < 4; ++c) {

@@ -261,6 +261,25 @@ __global__ void scatter_add_rows_kernel(const double* __restrict__ src, double* 
   }
 }
 
+// Number of elements with |t2ab[i][J][a][B] - t2ab[J][i][B][a]| > tol (n
+// occupied and v virtual of each spin); zero means the mixed amplitudes are
+// spin-flip symmetric to within tol.
+__global__ void t2ab_flip_mismatch(const double* __restrict__ t2ab, int n, int v, double tol,
+                                   unsigned int* __restrict__ count) {
+  const int64_t total = (int64_t)n * n * v * v;
+  unsigned int bad = 0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int B = (int)(idx % v);
+    int64_t r = idx / v;
+    const int a = (int)(r % v);
+    r /= v;
+    const int J = (int)(r % n), i = (int)(r / n);
+    if (!(fabs(t2ab[idx] - t2ab[(((int64_t)J * n + i) * v + B) * v + a]) <= tol)) ++bad;
+  }
+  if (bad) atomicAdd(count, bad);
+}
+
 inline int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
@@ -362,6 +381,14 @@ cudaError_t launch_scatter_add_rows(const double* src, double* dst, const int* l
   const int64_t n = (int64_t)nlist * row;
   if (n == 0) return cudaSuccess;
   scatter_add_rows_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, list, nlist, row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_t2ab_flip_mismatch(const double* t2ab, int n, int v, double tol,
+                                     unsigned int* count, cudaStream_t s) {
+  const int64_t total = (int64_t)n * n * v * v;
+  if (total == 0) return cudaSuccess;
+  t2ab_flip_mismatch<<<grid_for(total), 256, 0, s>>>(t2ab, n, v, tol, count);
   return cudaGetLastError();
 }
 
