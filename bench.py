@@ -386,6 +386,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--fp64-sample", type=int, default=2, help="FP64-path triplets per case")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--closed-shell", action="store_true",
+                    help="closed-shell domain (nocc of spin up for both spins, identical data); "
+                         "both spins passed as the same arrays, so the spin-flip images run once")
     ap.add_argument("--fov", action="store_true",
                     help="restricted open-shell domain: add an f_ov block (and time the "
                          "orbital contributions too)")
@@ -419,6 +422,9 @@ def main():
 
     cfg = dict(CONFIGS[args.config])
     cfg["seed"] = cfg["seed"] + 1000 * rank
+    if args.closed_shell:
+        cfg["nocc"] = (cfg["nocc"][0], cfg["nocc"][0])
+        cfg["closed_shell"] = True
     t_gen = time.time()
     dom = make_domain(**cfg)
     if args.fov:
@@ -439,6 +445,9 @@ def main():
                          f"{sec:.1f} s"}
 
     dd = lno_ot.to_device(dom, dev)
+    if args.closed_shell:  # the closed-shell calling form: one set of arrays for both spins
+        dd = dict(dd, B=[dd["B"][0]] * 2, eps=[dd["eps"][0]] * 2, t1=[dd["t1"][0]] * 2,
+                  t2bb=dd["t2aa"])
     ctx = lno_ot.Context(local, args.precision)
     alg = total_alg_flops(nocc, nbas)
 
@@ -553,7 +562,11 @@ def main():
         "precision": (f"{args.precision.upper()}: exact BF16 slices of float64 operands on "
                       f"tcgen05 (FP32 TMEM accumulators per weight class), float64 "
                       f"denominators and compensated sums"),
-        "config": {"workload": workload_name(args.config) + (" + f_ov (RO reference)" if args.fov else ""),
+        "config": {"workload": (f"single LNO domain E(T): nbas={nbas} nocc={nocc[0]}/{nocc[1]} "
+                                f"naux={dom['naux']}, closed shell (aaa, aab computed; bbb, abb "
+                                f"their spin-flip images)" if args.closed_shell
+                                else workload_name(args.config))
+                   + (" + f_ov (RO reference)" if args.fov else ""),
                    **cfg_public(cfg), **({"fov_sd": 0.02} if args.fov else {}),
                    "l2": f"inputs larger than L2 ({domain_bytes(nbas, nocc, dom['naux']) / 1e9:.1f} GB)",
                    "parallelism": f"replicas x{world} (one domain per GPU)"},
