@@ -381,7 +381,7 @@ def main():
     ap.add_argument("--c3-sample", type=int, default=8, help="domains of the c3 batch")
     ap.add_argument("--backward", action="store_true", help="time the adjoint on a sample")
     ap.add_argument("--bwd-sample", type=int, default=1, help="adjoint triplets per case")
-    ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x10", choices=["bf16x10", "bf16x6", "bf16x3"])
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle triplets per case")
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--fp64-sample", type=int, default=2, help="FP64-path triplets per case")

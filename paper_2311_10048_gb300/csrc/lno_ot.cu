@@ -737,6 +737,9 @@ struct SpinPass {
     if (R.S == 2)
       return pack_all(R.slices<2>(AT), R.slices<2>(BT), R.slices<2>(A1), R.slices<2>(BG),
                       R.slices<2>(BF), R.slices<2>(AT2));
+    if (R.S == 4)
+      return pack_all(R.slices<4>(AT), R.slices<4>(BT), R.slices<4>(A1), R.slices<4>(BG),
+                      R.slices<4>(BF), R.slices<4>(AT2));
     return pack_all(R.slices<3>(AT), R.slices<3>(BT), R.slices<3>(A1), R.slices<3>(BG),
                     R.slices<3>(BF), R.slices<3>(AT2));
   }
@@ -762,11 +765,17 @@ struct SpinPass {
         if (R.S == 2)
           CU(launch_tc_gemm_mc<2, 256, float>(mA64, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr,
                                               nsm, R.st));
+        else if (R.S == 4)
+          CU(launch_tc_gemm_mc<4, 128, float>(mA64, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr,
+                                              nsm, R.st));
         else
           CU(launch_tc_gemm_mc<3, 128, float>(mA64, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr,
                                               nsm, R.st));
       } else if (R.S == 2) {
         CU(launch_tc_gemm<2, 256, float>(mA, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr, nsm,
+                                         R.st));
+      } else if (R.S == 4) {
+        CU(launch_tc_gemm<4, 128, float>(mA, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr, nsm,
                                          R.st));
       } else {
         CU(launch_tc_gemm<3, 128, float>(mA, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr, nsm,
@@ -1075,7 +1084,7 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
   ctx->ev_used = 0;
   Run R(ctx, dom);
   R.f64 = ctx->prec == LNO_OT_FP64;
-  R.S = ctx->prec == LNO_OT_BF16X6 ? 3 : 2;
+  R.S = ctx->prec == LNO_OT_BF16X6 ? 3 : ctx->prec == LNO_OT_BF16X10 ? 4 : 2;
   CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
   cudaEvent_t t0 = R.event(), t1 = R.event(), t2 = R.event();
   if (t0) cudaEventRecord(t0, R.st);
@@ -1643,7 +1652,7 @@ extern "C" {
 
 int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
   if (!ctx || !opt) return LNO_OT_EINVAL;
-  if (opt->precision < 0 || opt->precision > 3) return LNO_OT_EINVAL;
+  if (opt->precision < 0 || opt->precision > 4) return LNO_OT_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
     cudaGetLastError();

@@ -30,7 +30,8 @@
 // Kernel structure (one CTA per SM, persistent over tiles of 128 x BN):
 //   warp 0      TMA producer (one thread), STAGES-deep smem ring
 //   warp 1      TMEM allocator and MMA issuer (one thread); S accumulators
-//               of 128 x BN FP32 (BN = 256 for S <= 2, 128 for S >= 3)
+//               of 128 x BN FP32 (BN = 256 for S <= 2, 128 for S >= 3; S = 4
+//               fills the 512 TMEM columns, so its epilogue is not overlapped)
 //   warps 2..5  epilogue: tcgen05.ld -> scale -> coalesced stores along m; when
 //               TMEM has room (S = 3, BN = 128) the combined tile is parked in
 //               spare columns so the next tile's MMAs overlap the stores
@@ -592,6 +593,12 @@ template cudaError_t launch_tc_gemm_mc<2, 256, float>(const CUtensorMap*, const 
 template cudaError_t launch_tc_gemm_mc<3, 128, float>(const CUtensorMap*, const CUtensorMap*,
                                                       const TcProb*, int, int, int, int, double,
                                                       int*, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_tc_gemm_mc<4, 128, float>(const CUtensorMap*, const CUtensorMap*,
+                                                      const TcProb*, int, int, int, int, double,
+                                                      int*, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_tc_gemm<4, 128, float>(const CUtensorMap*, const CUtensorMap*,
+                                                   const TcProb*, int, int, int, int, double, int*,
+                                                   unsigned long long*, int, cudaStream_t);
 
 template cudaError_t launch_tc_gemm<2, 256, float>(const CUtensorMap*, const CUtensorMap*,
                                                    const TcProb*, int, int, int, int, double, int*,

@@ -16,8 +16,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblno_ot.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "lno_ot.h")
 
 OK, EINVAL, EDEVICE, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-FP64, BF16X3, TF32, BF16X6 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "bf16x3": BF16X3, "tf32": TF32, "bf16x6": BF16X6}
+FP64, BF16X3, TF32, BF16X6, BF16X10 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "bf16x3": BF16X3, "tf32": TF32, "bf16x6": BF16X6,
+              "bf16x10": BF16X10}
 CASES = ("aaa", "aab", "abb", "bbb")
 
 

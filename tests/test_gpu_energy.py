@@ -216,3 +216,37 @@ def test_tuning_table_is_read(lib, tmp_path):
         assert e == ref                          # schedule changes never change the result
     with pytest.raises(lno_ot.LnoError):
         lno_ot.Context(0, "bf16x6", tune_cache=str(tmp_path / "missing.txt"))
+
+
+@pytest.fixture(scope="module")
+def ctx10(lib):
+    c = lno_ot.Context(0, "bf16x10")
+    yield c
+    c.close()
+
+
+def test_c0_bf16x10_within_1e8(ctx10):
+    g = golden("c0")
+    out, et = run_with_trip(ctx10, config_domain("c0"))
+    for i, c in enumerate(CASES):
+        assert np.abs(et[i] - np.array(g["cases"][c]["e"])).max() <= 1e-9, c
+    assert abs(out["total"] - g["total"]) <= 1e-8
+
+
+def test_c4_bf16x10_matches_stored_oracle(ctx10):
+    # 4 BF16 slices per operand: per triplet ~40x closer to the oracle than BF16X6
+    g = golden("c4")
+    out, et = run_with_trip(ctx10, config_domain("c4"))
+    for i, c in enumerate(CASES):
+        assert np.abs(et[i] - np.array(g["cases"][c]["e"])).max() <= 2e-9, c
+    assert abs(out["total"] - g["total"]) <= 1e-8
+
+
+@pytest.mark.parametrize("shape", SHAPES[:5])
+def test_shapes_bf16x10_vs_oracle(ctx10, shape):
+    nbas, na, nb, naux, seed = shape
+    d = make_domain(nbas, (na, nb), naux=naux, L=naux / 3, seed=seed, t1_sd=0.02)
+    out, _ = run_with_trip(ctx10, d)
+    ref = T.energy(d)
+    for c in CASES:
+        assert abs(out[c] - ref[c]) <= 1e-9 + 1e-9 * abs(ref[c]), c
