@@ -48,11 +48,13 @@ def peaks():
     return d
 
 
-# DRAM bytes (read + write) per tensor-core flop of the BF16X6 contraction,
-# from one ncu capture of that kernel on a c1-sized group (nbas 368, nocc
-# 8/6, naux 1200: 8.626 GB over 9 217 296 MMAs of 128x128x16); the per-launch
-# traffic scales with the launch's tensor flops at a fixed virtual space.
-DRAM_BYTES_PER_TENSOR_FLOP_X6 = 8.626e9 / (9217296 * 128 * 128 * 16 * 2)
+# DRAM bytes (read + write) per tensor-core flop of the contraction, from one
+# ncu capture per precision on a c1-sized group (nbas 368, nocc 8/6, naux
+# 1200): BF16X6 8.626 GB over 9 217 296 MMAs of 128x128x16, BF16X10 10.693 GB
+# over 15 362 160; the per-launch traffic scales with the launch's tensor flops
+# at a fixed virtual space.
+DRAM_BYTES_PER_TENSOR_FLOP = {"bf16x6": 8.626e9 / (9217296 * 128 * 128 * 16 * 2),
+                              "bf16x10": 10.693e9 / (15362160 * 128 * 128 * 16 * 2)}
 
 # FP32 operations per restricted (abc) element in the float32 energy kernel
 # (an FMA counts 2): W 2, V 17 (same spin) / 9 (mixed), W (W + V) 2,
@@ -543,8 +545,8 @@ def main():
     peak = pk.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
     launches = sum(s["contract_launches"] + s["energy_launches"] + s["other_launches"]
                    for s in stats)
-    traffic = (DRAM_BYTES_PER_TENSOR_FLOP_X6 * tc_flops_launch / 1e9
-               if args.precision == "bf16x6" else None)
+    bpf = DRAM_BYTES_PER_TENSOR_FLOP.get(args.precision)
+    traffic = bpf * tc_flops_launch / 1e9 if bpf else None
     # the float32 energy kernel is bound by the FP32 ALUs: peak = 152 SMs x 128
     # FP32 lanes x 2 flop (FMA) x the SM clock seen under load
     n_same, n_mixed = energy_elements(nocc, nbas)
