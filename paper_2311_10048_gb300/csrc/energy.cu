@@ -137,7 +137,6 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
     }
     // ---- V tables -----------------------------------------------------------
     {
-      const int nos = a.nos;
       if (!MIXED) {
         const int occ3[3][2] = {{tr.j, tr.k}, {tr.k, tr.i}, {tr.i, tr.j}};
         const int offs[3][2] = {{b0, c0}, {a0, c0}, {a0, b0}};
@@ -292,7 +291,7 @@ __global__ void energy_prep(EnergyArgs a, float* __restrict__ vt_out, int64_t vt
   const int g = blockIdx.y;
   const Trip tr = a.trips[g];
   float* out = vt_out + (int64_t)g * vt_stride;
-  const int nvs = a.nvs, nvt = a.nvt, nos = a.nos;
+  const int nvs = a.nvs, nvt = a.nvt;
   if (a.kind == SAME) {
     const int occ3[3][2] = {{tr.j, tr.k}, {tr.k, tr.i}, {tr.i, tr.j}};
     const int64_t n = 3LL * nvs * nvs;
