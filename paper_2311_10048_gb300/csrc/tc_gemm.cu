@@ -203,7 +203,6 @@ struct Cfg {
   static constexpr int kStage = S * (kABytes + kBBytes);
   static constexpr int kStages = (kSmemBudget - 2048) / kStage;
   static constexpr int kSmem = kStages * kStage + 1024 + 256;
-  static constexpr int kProducts = S * (S + 1) / 2;
   static_assert(kStages >= 2, "pipeline needs two stages");
   static_assert(S * BN <= 512, "one TMEM accumulator per weight class");
 };
@@ -444,37 +443,37 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
             if (amax != nullptr && m < M && n0 + j < N) lmax = fmaxf(lmax, fabsf(x));
           }
         }
-        continue;
-      }
+      } else {
 #pragma unroll 1
-      for (int c = 0; c < BN / 16; ++c) {
-        uint32_t acc[S][16];
+        for (int c = 0; c < BN / 16; ++c) {
+          uint32_t acc[S][16];
 #pragma unroll
-        for (int g = 0; g < S; ++g) tmem_ld16(tbase + g * BN + c * 16, acc[g]);
-        tmem_ld_wait();
-        const int n0 = nt * BN + c * 16;
-        OutT* op = out + (int64_t)n0 * ldo + m;
+          for (int g = 0; g < S; ++g) tmem_ld16(tbase + g * BN + c * 16, acc[g]);
+          tmem_ld_wait();
+          const int n0 = nt * BN + c * 16;
+          OutT* op = out + (int64_t)n0 * ldo + m;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          // lower classes first (each exact), then one rounding against HI
-          float lo = 0.f;
+          for (int j = 0; j < 16; ++j) {
+            // lower classes first (each exact), then one rounding against HI
+            float lo = 0.f;
 #pragma unroll
-          for (int g = S - 1; g >= 1; --g) lo = __fadd_rn(lo, __uint_as_float(acc[g][j]));
-          const float hi = __uint_as_float(acc[0][j]);
-          if constexpr (sizeof(OutT) == 4) {
-            const float v = __fmul_rn(__fadd_rn(hi, lo), fscale);
-            if (mok && n0 + j < N) op[(int64_t)j * ldo] = v;
-            if (amax != nullptr && m < M && n0 + j < N) lmax = fmaxf(lmax, fabsf(v));
-          } else {
-            if (mok && n0 + j < N)
-              op[(int64_t)j * ldo] = (double)__fmul_rn(hi, fscale) + (double)__fmul_rn(lo, fscale);
-            if (amax != nullptr && m < M && n0 + j < N)
-              lmax = fmaxf(lmax, fabsf(__fmul_rn(__fadd_rn(hi, lo), fscale)));
+            for (int g = S - 1; g >= 1; --g) lo = __fadd_rn(lo, __uint_as_float(acc[g][j]));
+            const float hi = __uint_as_float(acc[0][j]);
+            if constexpr (sizeof(OutT) == 4) {
+              const float v = __fmul_rn(__fadd_rn(hi, lo), fscale);
+              if (mok && n0 + j < N) op[(int64_t)j * ldo] = v;
+              if (amax != nullptr && m < M && n0 + j < N) lmax = fmaxf(lmax, fabsf(v));
+            } else {
+              if (mok && n0 + j < N)
+                op[(int64_t)j * ldo] = (double)__fmul_rn(hi, fscale) + (double)__fmul_rn(lo, fscale);
+              if (amax != nullptr && m < M && n0 + j < N)
+                lmax = fmaxf(lmax, fabsf(__fmul_rn(__fadd_rn(hi, lo), fscale)));
+            }
           }
         }
+        tc_fence_before();
+        mbar_arrive(tempty);
       }
-      tc_fence_before();
-      mbar_arrive(tempty);
     }
     if (amax != nullptr)
       atomicMax(amax, (unsigned long long)__double_as_longlong((double)lmax));
