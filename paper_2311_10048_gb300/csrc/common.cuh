@@ -64,6 +64,8 @@ struct EnergyArgs {
   int vmode;
   const double* t2ss;  // [nos][nos][nvs][nvs] t^{xy}_{pr} (vmode 1)
   const double* t2st;  // [nos][not][nvs][nvt] t^{xC}_{pK} (vmode 1, mixed)
+  const double* fs;    // [nos][nvs] f_ov of spin s (fused mixed pass only)
+  const double* ft;    // [not][nvt] f_ov of spin t (fused mixed pass only)
   const int3* blocks;  // cube tiles (A,B,C) of 16-blocks
   int nblocks;
   int pitch_x;         // row pitch (elements) of XT / YT (same: a; mixed: a)

@@ -358,11 +358,16 @@ __device__ __forceinline__ float div_nr(float num, float D) {
 //   T1[b][c][a] pitch 20 (float4 along a)   X[a,(bc)] / Y[a,(bC)]
 //   T2[a][c][b] pitch 18 (float2 along b)   X[b,(ac)] / Y[b,(aC)]
 //   T3[a][b][c] pitch 24                    X[c,(ab)] / Z'[C,(ab)]
-template <bool MIXED, bool FM>
+// FU (mixed spin only): V = V(T1) + V(f_ov) in one pass; the f_ov planes sit
+// vt_half floats after the T1 planes of each triplet's table and the f_ov
+// coefficients come from a.fs / a.ft.
+template <bool MIXED, bool FM, bool FU>
 __global__ void __launch_bounds__(256, 2)
 energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ Z,
-           const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt) {
+           const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt, int64_t vt_half) {
+  static_assert(!FU || (MIXED && !FM), "the fused f_ov pass is the mixed-spin W (W + V) sum");
   constexpr int P1 = 20, P2 = 18, P3 = 24;
+  constexpr int FT = FU ? TB : 1, FP = FU ? TP : 1;   // f_ov table sizes (1 when absent)
   __shared__ __align__(16) float T1[TB * TB * P1];
   __shared__ __align__(16) float T2[TB * TB * P2];
   __shared__ __align__(16) float T3[TB * TB * P3];
@@ -374,12 +379,20 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   __shared__ float tb_s[3][TB], tc_s[3][TB];
   __shared__ float ebh[2][TB], ebl[2][TB];
   __shared__ double red[8];
+  // f_ov planes (b,C): t^{bC}_{jK}, t^{bC}_{iK}; (a,C): t^{aC}_{jK}, t^{aC}_{iK};
+  // (a,b): t^{ab}_{ij}; coefficients f_ia, f_ja / f_ib, f_jb / f_KC
+  __shared__ float kbcf[2][FT][FP];
+  __shared__ __align__(8) float2 kacf[FT][FT];
+  __shared__ float kabf[FT][FT];
+  __shared__ __align__(8) float2 adf[FT];
+  __shared__ float tbf_s[2][FT], tcf_s[FT];
 
   const int g = blockIdx.y;
   const Trip tr = a.trips[g];
   const float* Xg = X + (int64_t)g * a.x_stride;
   const float* Zg = MIXED ? Z + (int64_t)g * a.z_stride : nullptr;
   const float* Vg = VT + (int64_t)g * vt_stride;
+  const float* Vf = Vg + vt_half;
   const int tid = threadIdx.x;
   const int r1 = tid / TB, r2 = tid % TB;           // row owned in the fetch phase
   const int lane = tid & 31, wid = tid >> 5;
@@ -393,6 +406,8 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   float4 xr[3][4];
   float vr[9];
   float t1r[3];
+  float vrf[FU ? 5 : 1];
+  float f1r[2];
   TwoF er;
   bool ok1 = false, ok2 = false, ok3 = false;
 
@@ -451,6 +466,17 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
       }
       const int x = a0 + r1, y = b0 + r2;
       vr[4] = (x < nvs && y < nvs) ? __ldg(Vg + 2LL * nvs * pvt + (int64_t)x * pv + y) : 0.f;
+      if constexpr (FU) {   // the same positions of the f_ov planes
+#pragma unroll
+        for (int pl = 0; pl < 2; ++pl) {
+          const int xx = rows[pl] + r1, yy = c0 + r2;
+          const bool in = xx < nvs && yy < nvt;
+#pragma unroll
+          for (int o = 0; o < 2; ++o)
+            vrf[pl * 2 + o] = in ? __ldg(Vf + ((int64_t)o * nvs + xx) * pvt + yy) : 0.f;
+        }
+        vrf[4] = (x < nvs && y < nvs) ? __ldg(Vf + 2LL * nvs * pvt + (int64_t)x * pv + y) : 0.f;
+      }
     }
     if (tid < 3 * TB) {
       const int bl = tid / TB, l = tid % TB;
@@ -466,9 +492,17 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
         t1r[0] = x < nvs ? (float)a.t1s[(int64_t)tr.i * nvs + x] : 0.f;
         t1r[1] = x < nvs ? (float)a.t1s[(int64_t)tr.j * nvs + x] : 0.f;
         t1r[2] = 0.f;
+        if constexpr (FU) {
+          f1r[0] = x < nvs ? (float)a.fs[(int64_t)tr.i * nvs + x] : 0.f;
+          f1r[1] = x < nvs ? (float)a.fs[(int64_t)tr.j * nvs + x] : 0.f;
+        }
       } else {
         t1r[0] = x < nvt ? (float)a.t1t[(int64_t)tr.k * nvt + x] : 0.f;
         t1r[1] = t1r[2] = 0.f;
+        if constexpr (FU) {
+          f1r[0] = x < nvt ? (float)a.ft[(int64_t)tr.k * nvt + x] : 0.f;
+          f1r[1] = 0.f;
+        }
       }
       const double* e = tblock ? a.eps_t : a.eps_s;
       const int no = tblock ? a.not_ : a.nos;
@@ -504,17 +538,30 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
         kbc[0][r1][r2] = vr[0]; kbc[1][r1][r2] = vr[1];
         kac[r1][r2] = make_float4(vr[2], vr[3], 0.f, 0.f);
         kab[r1][r2] = make_float4(vr[4], 0.f, 0.f, 0.f);
+        if constexpr (FU) {
+          kbcf[0][r1][r2] = vrf[0]; kbcf[1][r1][r2] = vrf[1];
+          kacf[r1][r2] = make_float2(vrf[2], vrf[3]);
+          kabf[r1][r2] = vrf[4];
+        }
       }
       if (tid < 3 * TB) {
         const int bl = tid / TB, l = tid % TB;
         if (bl == 0) {
           ad[l] = make_float4(t1r[0], t1r[1], t1r[2], er.hi);
           ael[l] = er.lo;
+          if constexpr (FU) adf[l] = make_float2(f1r[0], f1r[1]);
         } else {
           float* tt = bl == 1 ? &tb_s[0][0] : &tc_s[0][0];
           tt[l] = t1r[0]; tt[TB + l] = t1r[1]; tt[2 * TB + l] = t1r[2];
           ebh[bl - 1][l] = er.hi;
           ebl[bl - 1][l] = er.lo;
+          if constexpr (FU) {
+            if (bl == 1) {
+              tbf_s[0][l] = f1r[0]; tbf_s[1][l] = f1r[1];
+            } else {
+              tcf_s[l] = f1r[0];
+            }
+          }
         }
       }
     }
@@ -527,6 +574,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
       bool rowok[2];
       TwoF dbc[2];
       float k0[2], k1[2], k2[2], tb0[2], tb1[2], tb2[2];
+      float kf0[2] = {0.f, 0.f}, kf1[2] = {0.f, 0.f}, tbf0[2] = {0.f, 0.f}, tbf1[2] = {0.f, 0.f};
 #pragma unroll
       for (int sb = 0; sb < 2; ++sb) {
         const int bl = bl0 + sb, b = b0 + bl;
@@ -534,8 +582,13 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
         dbc[sb] = df_sub(df_sub(eocc, TwoF{ebh[0][bl], ebl[0][bl]}), TwoF{ebh[1][cl], ebl[1][cl]});
         k0[sb] = kbc[0][bl][cl]; k1[sb] = kbc[1][bl][cl]; k2[sb] = kbc[2][bl][cl];
         tb0[sb] = tb_s[0][bl]; tb1[sb] = tb_s[1][bl]; tb2[sb] = tb_s[2][bl];
+        if constexpr (FU) {
+          kf0[sb] = kbcf[0][bl][cl]; kf1[sb] = kbcf[1][bl][cl];
+          tbf0[sb] = tbf_s[0][bl]; tbf1[sb] = tbf_s[1][bl];
+        }
       }
       const float tc0 = tc_s[0][cl], tc1 = tc_s[1][cl], tc2 = tc_s[2][cl];
+      const float tcf0 = FU ? tcf_s[cl] : 0.f;
       // last a (exclusive) any element of this thread can use: a < b <= b0+bl0+1
       const int aend = min(al0 + 8, b0 + bl0 + 1 - a0);
       if ((rowok[0] || rowok[1]) && aend > al0) {
@@ -560,6 +613,11 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
             const float2 x2 = *reinterpret_cast<const float2*>(T2 + (al * TB + cl) * P2 + bl0);
             const float4 vac = kac[al][cl];
             const float x2a[2] = {x2.x, x2.y};
+            float2 daf = make_float2(0.f, 0.f), vacf = make_float2(0.f, 0.f);
+            if constexpr (FU) {
+              daf = adf[al];
+              vacf = kacf[al][cl];
+            }
 #pragma unroll
             for (int sb = 0; sb < 2; ++sb) {
               const int bl = bl0 + sb;
@@ -567,8 +625,11 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
               const float x3 = T3[(al * TB + bl) * P3 + cl];
               const float vab = kab[al][bl].x;
               const float w = x1a[sb][u] - x2a[sb] + x3;
-              const float v = da.x * k0[sb] - da.y * k1[sb] - tb0[sb] * vac.x +
-                              tb1[sb] * vac.y + tc0 * vab;
+              float v = da.x * k0[sb] - da.y * k1[sb] - tb0[sb] * vac.x +
+                        tb1[sb] * vac.y + tc0 * vab;
+              if constexpr (FU)   // the f_ov term: f for t1, the doubles for the integrals
+                v += daf.x * kf0[sb] - daf.y * kf1[sb] - tbf0[sb] * vacf.x +
+                     tbf1[sb] * vacf.y + tcf0 * kabf[al][bl];
               const float num = FM ? __fmul_rn(w, v) : __fmul_rn(w, __fadd_rn(w, v));
               float s, e;
               two_sum(dbc[sb].hi, -da.w, s, e);
@@ -749,14 +810,14 @@ cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* 
   dim3 grid(nchunks, ntrip);
   if (a.kind == SAME) {
     if (a.vmode)
-      energy_f32<false, true><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+      energy_f32<false, true, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0);
     else
-      energy_f32<false, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+      energy_f32<false, false, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0);
   } else {
     if (a.vmode)
-      energy_f32<true, true><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+      energy_f32<true, true, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0);
     else
-      energy_f32<true, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt);
+      energy_f32<true, false, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0);
   }
   return cudaGetLastError();
 }
@@ -768,6 +829,26 @@ cudaError_t launch_group(const EnergyArgs& a, const void* X, const void* Z, dim3
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k<<<grid, 256, sm, st>>>(a, (const T*)X, (const T*)Z);
+  return cudaGetLastError();
+}
+
+// Mixed spin with the f_ov term in one pass: T1 planes in [0, vt_half) and
+// f_ov planes in [vt_half, 2 vt_half) of each triplet's table (stride
+// 2 vt_half); a.t1s/t1t and a.fs/ft the two coefficient sets.
+cudaError_t launch_energy_f32_fused(const EnergyArgs& a, const float* X, const float* Z,
+                                   float* vtab, int64_t vt_half, int pv, int pvt, int ntrip,
+                                   int nchunks, cudaStream_t st) {
+  if (ntrip <= 0) return cudaSuccess;
+  if (a.kind == SAME) return cudaErrorInvalidValue;
+  dim3 gp(64, ntrip);
+  EnergyArgs a0 = a, a1 = a;
+  a0.vmode = 0;
+  a1.vmode = 1;
+  energy_prep<<<gp, 256, 0, st>>>(a0, vtab, 2 * vt_half, pv, pvt);
+  energy_prep<<<gp, 256, 0, st>>>(a1, vtab + vt_half, 2 * vt_half, pv, pvt);
+  dim3 grid(nchunks, ntrip);
+  energy_f32<true, false, true><<<grid, 256, 0, st>>>(a0, X, Z, vtab, 2 * vt_half, pv, pvt,
+                                                      vt_half);
   return cudaGetLastError();
 }
 

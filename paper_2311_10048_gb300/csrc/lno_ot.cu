@@ -35,6 +35,9 @@ cudaError_t launch_energy(const EnergyArgs& a, const void* X, const void* Z, boo
 cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* Z, float* vtab,
                               int64_t vt_stride, int pv, int pvt, int ntrip, int nchunks,
                               cudaStream_t st);
+cudaError_t launch_energy_f32_fused(const EnergyArgs& a, const float* X, const float* Z,
+                                   float* vtab, int64_t vt_half, int pv, int pvt, int ntrip,
+                                   int nchunks, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partial, int np, const double* partial2,
                                    int ntrip, double* e_trip, cudaStream_t st);
 cudaError_t launch_orbital_partition(const OrbPartArgs& A, cudaStream_t st);
@@ -860,8 +863,11 @@ struct SpinPass {
     const int pv = (int)round_up(std::max(v, 1), 16), pvt = (int)round_up(std::max(vt, 1), 16);
     const int64_t vt_stride = is_mixed ? round_up(2LL * v * pvt + (int64_t)v * pv, 16)
                                        : 3LL * v * pv;
+    // mixed spin on the tensor-core path takes the f_ov term in the same pass
+    // (T1 and f_ov planes side by side in the V table); elsewhere a second pass
+    const bool fuse = fov && !f64 && is_mixed;
     float* vtab = nullptr;
-    if (!f64) TRY(A.get(&vtab, (size_t)(G * vt_stride)));
+    if (!f64) TRY(A.get(&vtab, (size_t)(G * vt_stride * (fuse ? 2 : 1))));
     ProbF64* dpf = nullptr;
     TcProb* dpt = nullptr;
     if (f64) {
@@ -992,14 +998,25 @@ struct SpinPass {
       ea.partial = partial;
       cudaEvent_t e0 = R.event(), e1 = R.event();
       if (e0) cudaEventRecord(e0, R.st);
-      if (f64)
+      if (f64) {
         CU(launch_energy(ea, X, Z, f64, ng, P, R.st));
-      else
+      } else if (fuse) {
+        EnergyArgs ef = ea;
+        ef.fs = R.fov[s];
+        ef.ft = R.fov[t];
+        ef.t2ss = t2ss;
+        ef.t2st = t2st;
+        CU(launch_energy_f32_fused(ef, reinterpret_cast<const float*>(X),
+                                   reinterpret_cast<const float*>(Z), vtab, vt_stride, pv, pvt,
+                                   ng, P, R.st));
+        R.stats->energy_launches += 1;
+      } else {
         CU(launch_energy_f32(ea, reinterpret_cast<const float*>(X),
                              reinterpret_cast<const float*>(Z), vtab, vt_stride, pv, pvt, ng, P,
                              R.st));
+      }
       double* partial2 = nullptr;
-      if (fov) {
+      if (fov && !fuse) {
         // the f_ov part of V in a second pass over the same X (and Z'):
         // sum W V_f / D with V_f built like the T1 term from f_ov and T2
         EnergyArgs ef = ea;
