@@ -97,7 +97,7 @@ def test_c2_sampled_parity_both_paths(lib):
     del ev, dt
     dd = lno_ot.to_device(d)
     res = {}
-    for prec, tol in (("fp64", 1e-8), ("bf16x6", 1e-7)):
+    for prec, tol in (("fp64", 1e-8), ("bf16x10", 1e-8), ("bf16x6", 1e-7)):
         et = [torch.zeros(len(s), dtype=torch.float64, device="cuda") for s in sel]
         ctx = lno_ot.Context(0, prec)
         ctx.energy(dd, e_trip=et, trip_sel=sel)
