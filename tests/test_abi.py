@@ -71,3 +71,20 @@ def test_ctypes_struct_layouts_match_c(tmp_path):
 def test_build_is_sm103a_only():
     from paper_2311_10048_gb300 import build as b
     assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_enum_values_match_binding():
+    """Status codes and precision modes: header enums vs the binding's constants."""
+    import re
+    text = open(os.path.join(ROOT, "include", "lno_ot.h")).read()
+    enums = {m.group(1): int(m.group(2))
+             for m in re.finditer(r"\b(LNO_OT_[A-Z0-9]+)\s*=\s*(-?\d+)", text)}
+    want = {"LNO_OT_OK": lno_ot.OK, "LNO_OT_EINVAL": lno_ot.EINVAL,
+            "LNO_OT_EDEVICE": lno_ot.EDEVICE, "LNO_OT_ENOMEM": lno_ot.ENOMEM,
+            "LNO_OT_ECUDA": lno_ot.ECUDA, "LNO_OT_ETIMEOUT": lno_ot.ETIMEOUT,
+            "LNO_OT_EUNSUPPORTED": lno_ot.EUNSUPPORTED, "LNO_OT_FP64": lno_ot.FP64,
+            "LNO_OT_BF16X3": lno_ot.BF16X3, "LNO_OT_TF32": lno_ot.TF32,
+            "LNO_OT_BF16X6": lno_ot.BF16X6, "LNO_OT_BF16X10": lno_ot.BF16X10}
+    for k, v in want.items():
+        assert enums.get(k) == v, (k, enums.get(k), v)
+    assert set(lno_ot.PRECISIONS.values()) == {0, 1, 2, 3, 4}
