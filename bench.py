@@ -1,8 +1,20 @@
 """Benchmark: open-shell domain E(T) on GB300 through the lno_ot C ABI.
 
-One step = one full E(T) of the medium single domain (nbas 400, 40/38
-occupied, naux 1200; every stage of the hot path: DF assembly, operand
-layout, W/V contractions, energy reduction) with inputs resident in HBM.
+Workload: the medium single domain (nbas 400, 40/38 occupied, naux 1200).
+The K timed steps together compute the whole domain exactly once: step s is
+one lno_ot_energy call over block s of K of every spin case's restricted
+triplets (contiguous in the lexicographic triplet order), and runs every
+stage of the hot path for that block (staging, DF assembly, operand layout,
+W/V contractions, energy reduction) with the inputs resident in HBM.  The
+warm-up steps repeat the first blocks.  After the timed region:
+  * e2e: a few steps through the same call with the inputs copied from pinned
+    host memory inside the timed region;
+  * the float64 GPU path on a seeded triplet sample (the comparator);
+  * the whole domain once more in BF16X15 (8 more bits per operand slice in
+    the W contractions and the DF assembly), which measures the domain-total
+    error of the timed precision, with the BF16X15 error itself bounded by the
+    float64 sample;
+  * the CPU oracle on a bounded triplet sample (cpu_baseline and parity).
 
 Prints ONE JSON line (rank 0).  Under torchrun each rank computes its own
 domain of the same shape (seed + rank): weak scaling, no data-path
@@ -48,13 +60,13 @@ def peaks():
     return d
 
 
-# DRAM bytes (read + write) per tensor-core flop of the contraction, from one
-# ncu capture per precision on a c1-sized group (nbas 368, nocc 8/6, naux
-# 1200): BF16X6 8.626 GB over 9 217 296 MMAs of 128x128x16, BF16X10 10.693 GB
-# over 15 362 160; the per-launch traffic scales with the launch's tensor flops
-# at a fixed virtual space.
-DRAM_BYTES_PER_TENSOR_FLOP = {"bf16x6": 8.626e9 / (9217296 * 128 * 128 * 16 * 2),
-                              "bf16x10": 10.693e9 / (15362160 * 128 * 128 * 16 * 2)}
+# DRAM bytes (read + write) per tensor-core flop of the contraction kernel as
+# it is now, from one ncu capture per precision on a c1-sized group (filled in
+# from the capture named in the profiles folder; None = not captured since the
+# kernel last changed, and the line then reports traffic null).  The
+# per-launch traffic scales with the launch's tensor flops at a fixed virtual
+# space.
+DRAM_BYTES_PER_TENSOR_FLOP = {}
 
 # FP32 operations per restricted (abc) element in the float32 energy kernel
 # (an FMA counts 2): W 2, V 17 (same spin) / 9 (mixed), W (W + V) 2,
@@ -197,22 +209,50 @@ def cpu_oracle_sample(dom, sel, max_seconds=30.0):
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle, as it stands, on a bounded sample."""
+    """Reference arm: the CPU oracle, as it stands, one triplet per step.
+
+    Step s evaluates one seeded triplet of the workload (the cases in turn);
+    W untimed warm-up steps, then K timed steps.  The oracle's lazily built
+    integral cache is emptied before every step so that each step pays for
+    the whole triplet and the host memory stays bounded."""
+    import torch
+    from oracle.triples import Evaluator, triplets
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     cfg = dict(CONFIGS[args.config])
     dom = make_domain(**cfg)
-    sel = sample_triplets(dom["nocc"], args.cpu_sample)
-    vals, sec, flops, cores = cpu_oracle_sample(dom, sel, max_seconds=args.cpu_seconds)
+    torch.set_num_threads(os.cpu_count() or 1)
+    na, nb = dom["nocc"]
     nsteps = max(1, args.steps)
+    sel = sample_triplets(dom["nocc"], (nsteps + args.warmup + 3) // 4 + 1, seed=29)
+    order = [(ci, int(q)) for k in range(max(len(x) for x in sel))
+             for ci in range(4) if k < len(sel[ci]) for q in [sel[ci][k]]]
+    ev = Evaluator(dom)
+    trs = {c: triplets(c, na, nb) for c in CASES}
+    times, flops, counts = [], 0.0, {c: 0 for c in CASES}
+    with torch.no_grad():
+        for st in range(args.warmup + nsteps):
+            ci, q = order[st % len(order)]
+            c = CASES[ci]
+            ev._cache.clear()
+            t0 = time.perf_counter()
+            ev.triplet_energy(c, trs[c][q])
+            dt = time.perf_counter() - t0
+            if st >= args.warmup:
+                times.append(dt)
+                flops += alg_flops_triplet(c, dom["nocc"], dom["nbas"])
+                counts[c] += 1
+    sec = sum(times)
     value = flops / sec / 1e12
-    ntr = sum(len(v) for v in vals.values())
-    sample = f"{ntr} triplets of {args.config} ({', '.join(f'{c}:{len(vals[c])}' for c in CASES)})"
+    cores = torch.get_num_threads()
+    sample = (f"{nsteps} seeded triplets of {args.config}, one per step "
+              f"({', '.join(f'{c}:{counts[c]}' for c in CASES)}), after {args.warmup} warm-up "
+              f"triplets")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": nsteps, "warmup": args.warmup,
-        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": sec * 1e3 / nsteps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args.config), **cfg_public(cfg)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -373,43 +413,31 @@ def run_backward(args):
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c1", choices=sorted(CONFIGS) + ["custom", "c3"])
-    ap.add_argument("--c3-sample", type=int, default=8, help="domains of the c3 batch")
-    ap.add_argument("--backward", action="store_true", help="time the adjoint on a sample")
-    ap.add_argument("--bwd-sample", type=int, default=1, help="adjoint triplets per case")
-    ap.add_argument("--precision", default="bf16x10", choices=["bf16x10", "bf16x6", "bf16x3"])
-    ap.add_argument("--cpu-sample", type=int, default=2, help="oracle triplets per case")
-    ap.add_argument("--cpu-seconds", type=float, default=30.0)
-    ap.add_argument("--fp64-sample", type=int, default=2, help="FP64-path triplets per case")
-    ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--closed-shell", action="store_true",
-                    help="closed-shell domain (nocc of spin up for both spins, identical data); "
-                         "both spins passed as the same arrays, so the spin-flip images run once")
-    ap.add_argument("--fov", action="store_true",
-                    help="restricted open-shell domain: add an f_ov block (and time the "
-                         "orbital contributions too)")
-    ap.add_argument("--shape", default=None,
-                    help="custom domain nbas,nalpha,nbeta,naux (recipe of the configs, seed 5)")
-    args = ap.parse_args()
-    if args.shape:
-        nbas_, na_, nb_, naux_ = (int(x) for x in args.shape.split(","))
-        CONFIGS["custom"] = dict(nbas=nbas_, nocc=(na_, nb_), naux=naux_, L=naux_ / 4.0, seed=5)
-        args.config = "custom"
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.config == "c3":
-        return run_c3(args)
-    if args.backward:
-        return run_backward(args)
+def step_blocks(nocc, K):
+    """trip_sel of each of K steps: block s of every case's triplets."""
+    out = []
+    for st in range(K):
+        sel = []
+        for c in CASES:
+            n = ntrip(c, nocc)
+            sel.append(np.arange(n * st // K, n * (st + 1) // K, dtype=np.int64))
+        out.append(sel)
+    return out
 
+
+def sel_flops(sel, nocc, nbas):
+    return sum(alg_flops_triplet(c, nocc, nbas) * len(sel[ci]) for ci, c in enumerate(CASES))
+
+
+def err_stats(d):
+    d = np.asarray(d, dtype=np.float64)
+    if d.size == 0:
+        return None
+    return {"n": int(d.size), "max_abs_Eh": float(np.abs(d).max()), "mean_Eh": float(d.mean()),
+            "sd_Eh": float(d.std(ddof=1)) if d.size > 1 else 0.0}
+
+
+def run_domain(args):
     import torch
     import torch.distributed as dist
     from paper_2311_10048_gb300 import lno_ot
@@ -433,16 +461,20 @@ def main():
         dom = add_fov(dom, sd=0.02, seed=cfg["seed"])
     t_gen = time.time() - t_gen
     nbas, nocc = dom["nbas"], dom["nocc"]
-    sel = sample_triplets(nocc, args.cpu_sample)
+    K = max(1, args.steps)
+    blocks = step_blocks(nocc, K)
+    ntr = [ntrip(c, nocc) for c in CASES]
+    N_all = sum(ntr)
 
     # CPU baseline (rank 0, single GPU only): the oracle on a bounded sample
     cpu = None
     oracle_vals = None
+    sel_cpu = sample_triplets(nocc, args.cpu_sample)
     if rank == 0 and world == 1 and args.cpu_sample > 0:
-        oracle_vals, sec, flops, cores = cpu_oracle_sample(dom, sel, args.cpu_seconds)
-        ntr = sum(len(v) for v in oracle_vals.values())
+        oracle_vals, sec, flops, cores = cpu_oracle_sample(dom, sel_cpu, args.cpu_seconds)
+        nor = sum(len(v) for v in oracle_vals.values())
         cpu = {"value": flops / sec / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{ntr} seeded triplets of the same domain "
+               "sample": f"{nor} seeded triplets of the same domain "
                          f"({', '.join(f'{c}:{len(oracle_vals[c])}' for c in CASES)}), "
                          f"{sec:.1f} s"}
 
@@ -452,37 +484,38 @@ def main():
                   t2bb=dd["t2aa"])
     ctx = lno_ot.Context(local, args.precision)
     alg = total_alg_flops(nocc, nbas)
-
-    # warm-up (the last one also returns per-triplet contributions for parity)
-    et = [torch.zeros(max(ntrip(c, nocc), 1), dtype=torch.float64, device=dev) for c in CASES]
+    # per-triplet contributions of the whole domain, written block by block
+    et = [torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in ntr]
     eorb = ([torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in nocc]
             if args.fov else None)
-    for w in range(args.warmup):
-        out = ctx.energy(dd, e_trip=et if w == args.warmup - 1 else None, e_orb=eorb)
-    torch.cuda.synchronize()
-    parity = None
-    if oracle_vals is not None:
-        errs = []
-        for ci, c in enumerate(CASES):
-            got = et[ci].cpu().numpy()
-            for q, ref in zip(sel[ci], oracle_vals[c]):
-                errs.append(abs(float(got[int(q)]) - ref))
-        parity = {"sampled_triplets": len(errs), "max_abs_dE_per_triplet_Eh": max(errs),
-                  "tolerance_Eh": 1e-7}
 
-    # timed region: K steps, device-resident inputs
+    def views(sel):
+        return [et[ci][sel[ci][0]:sel[ci][-1] + 1] if len(sel[ci]) else None
+                for ci in range(4)]
+
+    def step(st, **kw):
+        sel = blocks[st % K]
+        if args.closed_shell and K == 1:   # whole domain: the spin-flip shortcut applies
+            return ctx.energy(dd, e_trip=views(sel), e_orb=eorb, **kw)
+        return ctx.energy(dd, e_trip=views(sel), trip_sel=sel, e_orb=eorb, **kw)
+
+    for w in range(args.warmup):
+        step(w)
+    torch.cuda.synchronize()
+
+    # timed region: K steps = the whole domain once, device-resident inputs
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    st = torch.cuda.current_stream()
+    st_ = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stats = []
+    stats, outs = [], []
     with ClockSampler(local) as clk:
-        e0.record(st)
-        for _ in range(args.steps):
-            out = ctx.energy(dd, e_orb=eorb)
+        e0.record(st_)
+        for s_ in range(K):
+            outs.append(step(s_))
             stats.append(ctx.stats())
-        e1.record(st)
+        e1.record(st_)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -491,56 +524,111 @@ def main():
     if world > 1:
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
     ms_max = float(t_local.item())
-    ms_step = ms_max / args.steps
-    value = alg * world * args.steps / (ms_max / 1e3) / 1e12
+    ms_step = ms_max / K
+    value = alg * world / (ms_max / 1e3) / 1e12
     clocks = clk.summary()
+    e_case = {c: math.fsum(o[c] for o in outs) for c in CASES}
+    e_case["total"] = math.fsum(e_case[c] for c in CASES)
+    et_host = [x[:n].cpu().numpy() for x, n in zip(et, ntr)]
 
-    # end to end: host (pinned) inputs -> device -> E(T) -> host, per step
-    host = {k: dom[k] for k in ("B", "eps", "t1", "t2aa", "t2bb", "t2ab")
-            + (("fov",) if args.fov else ())}
-    pinned = {}
-    h2d = 0
-    for k, v in host.items():
-        if isinstance(v, list):
-            pinned[k] = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in v]
-            h2d += sum(int(x.size) * 8 for x in v)
-        else:
-            pinned[k] = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
-            h2d += int(v.size) * 8
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    out_e2e = None
-    for _ in range(args.e2e_steps):
-        dn = dict(nbas=nbas, naux=dom["naux"], nocc=nocc)
-        for k, v in pinned.items():
-            dn[k] = ([x.to(dev, non_blocking=True) for x in v] if isinstance(v, list)
-                     else v.to(dev, non_blocking=True))
+    parity = None
+    if oracle_vals is not None:
+        errs = []
+        for ci, c in enumerate(CASES):
+            for q, ref in zip(sel_cpu[ci], oracle_vals[c]):
+                errs.append(abs(float(et_host[ci][int(q)]) - ref))
+        parity = {"sampled_triplets": len(errs), "max_abs_dE_per_triplet_Eh": max(errs),
+                  "tolerance_Eh": 1e-8, "vs": "CPU oracle"}
+
+    # end to end: host (pinned) inputs -> device -> E(T) of the step's block -> host
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {k: dom[k] for k in ("B", "eps", "t1", "t2aa", "t2bb", "t2ab")
+                + (("fov",) if args.fov else ())}
+        pinned, h2d = {}, 0
+        for k, v in host.items():
+            if isinstance(v, list):
+                pinned[k] = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in v]
+                h2d += sum(int(x.size) * 8 for x in v)
+            else:
+                pinned[k] = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+                h2d += int(v.size) * 8
         torch.cuda.synchronize()
-        out_e2e = ctx.energy(dn, e_orb=eorb)   # returns after the result is on the host
-        del dn
-    e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
+        fl = 0.0
+        t0 = time.perf_counter()
+        for s_ in range(args.e2e_steps):
+            dn = dict(nbas=nbas, naux=dom["naux"], nocc=nocc)
+            for k, v in pinned.items():
+                dn[k] = ([x.to(dev, non_blocking=True) for x in v] if isinstance(v, list)
+                         else v.to(dev, non_blocking=True))
+            sel = blocks[s_ % K]
+            ctx.energy(dn, trip_sel=sel)        # returns after the result is on the host
+            fl += sel_flops(sel, nocc, nbas)
+            del dn
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": fl / args.e2e_steps / e2e_s / 1e12, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 40,
+               "steps": args.e2e_steps, "seconds_per_step": e2e_s,
+               "what": "lno_ot_energy on one step's triplet block; every step copies the whole "
+                       "domain's inputs from pinned host memory and reads the 5 energies back"}
     ctx.close()
 
-    # plain FP64 GPU path on a sample of triplets (same domain, same GPU)
-    fp64 = None
+    # plain FP64 GPU path on a seeded triplet sample (same domain, same GPU)
+    fp64, e64 = None, None
+    fsel = sample_triplets(nocc, args.fp64_sample, seed=11)
     if args.fp64_sample > 0:
-        fsel = sample_triplets(nocc, args.fp64_sample, seed=11)
         c64 = lno_ot.Context(local, "fp64")
-        c64.energy(dd, trip_sel=fsel)                   # warm-up
-        r64 = c64.energy(dd, trip_sel=fsel)
+        et64 = [torch.zeros(max(len(x), 1), dtype=torch.float64, device=dev) for x in fsel]
+        c64.energy(dd, trip_sel=fsel, e_trip=et64)
         s64 = c64.stats()
         c64.close()
-        fl = sum(alg_flops_triplet(c, nocc, nbas) * len(fsel[ci]) for ci, c in enumerate(CASES))
+        e64 = [x[:len(q)].cpu().numpy() for x, q in zip(et64, fsel)]
+        fl = sel_flops(fsel, nocc, nbas)
         kern_ms = s64["ms_contract"] + s64["ms_energy"]
-        fp64 = {"value": fl / (kern_ms / 1e3) / 1e12, "unit": UNIT,
-                "sample": f"{sum(len(x) for x in fsel)} seeded triplets (contraction + energy "
-                          f"kernels; its float64 DF assembly excluded)",
-                "speedup_of_mixed": value / world / (fl / (kern_ms / 1e3) / 1e12)}
+        v64 = fl / (kern_ms / 1e3) / 1e12
+        fp64 = {"value": v64, "unit": UNIT,
+                "value_whole_call": fl / (s64["ms_total"] / 1e3) / 1e12,
+                "sample": f"{sum(len(x) for x in fsel)} seeded triplets ({args.fp64_sample} per "
+                          f"case); value = contraction + energy kernels, value_whole_call adds "
+                          f"its float64 DF assembly of the orbitals the sample uses",
+                "speedup_of_timed_precision": value / world / v64}
+        d = [et_host[ci][fsel[ci]] - e64[ci] for ci in range(4)]
+        fp64["timed_precision_minus_fp64_per_triplet"] = err_stats(np.concatenate(d))
+
+    # domain-total error: the whole domain again in BF16X15
+    accuracy = None
+    if args.ref_precision != "none" and args.precision != args.ref_precision:
+        cref = lno_ot.Context(local, args.ref_precision)
+        etr = [torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in ntr]
+        t0 = time.perf_counter()
+        outr = cref.energy(dd, e_trip=etr)
+        t_ref = time.perf_counter() - t0
+        cref.close()
+        etr_h = [x[:n].cpu().numpy() for x, n in zip(etr, ntr)]
+        diff = {c: math.fsum((et_host[ci] - etr_h[ci]).tolist()) for ci, c in enumerate(CASES)}
+        dtot = math.fsum(diff.values())
+        accuracy = {"reference": args.ref_precision.upper(), "reference_seconds": t_ref,
+                    "reference_energy_Eh": outr["total"],
+                    "timed_minus_reference_Eh": {**diff, "total": dtot},
+                    "max_abs_per_triplet_Eh": float(max(np.abs(et_host[ci] - etr_h[ci]).max()
+                                                        for ci in range(4) if ntr[ci]))}
+        if e64 is not None:
+            dr = np.concatenate([etr_h[ci][fsel[ci]] - e64[ci] for ci in range(4)])
+            stt = err_stats(dr)
+            # the reference's own domain-total error, from the float64 sample:
+            # N (|mean| + 3 sd / sqrt(n)) over all N triplets of the domain
+            ref_bound = N_all * (abs(stt["mean_Eh"]) + 3 * stt["sd_Eh"] / math.sqrt(stt["n"]))
+            accuracy["reference_minus_fp64_per_triplet"] = stt
+            accuracy["reference_total_error_bound_Eh"] = ref_bound
+            accuracy["domain_total_abs_dE_bound_Eh"] = abs(dtot) + ref_bound
+            accuracy["meets_1e-7_Eh"] = abs(dtot) + ref_bound <= 1e-7
 
     pk = peaks()
-    s_last = stats[-1]
-    tc_launch_ms = s_last["ms_contract"] / max(1, s_last["contract_launches"])
-    tc_flops_launch = s_last["tensor_flops"] / max(1, s_last["contract_launches"])
+    tot = {k: sum(s[k] for s in stats) for k in ("ms_contract", "ms_energy", "ms_stage",
+                                                  "ms_total", "tensor_flops")}
+    nlaunch = sum(s["contract_launches"] for s in stats)
+    tc_launch_ms = tot["ms_contract"] / max(1, nlaunch)
+    tc_flops_launch = tot["tensor_flops"] / max(1, nlaunch)
     achieved = tc_flops_launch / (tc_launch_ms / 1e3) / 1e12
     peak = pk.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
     launches = sum(s["contract_launches"] + s["energy_launches"] + s["other_launches"]
@@ -555,47 +643,49 @@ def main():
                          + n_mixed * ENERGY_FLOPS_PER_ELEMENT["mixed"])
     mhz = clocks.get("sm_mhz") or 2070.0
     en_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
-    en_achieved = en_flops / (s_last["ms_energy"] / 1e3) / 1e12
+    en_achieved = en_flops / (tot["ms_energy"] / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16", "data": "synthetic",
         "precision": (f"{args.precision.upper()}: exact BF16 slices of float64 operands on "
                       f"tcgen05 (FP32 TMEM accumulators per weight class), float64 "
                       f"denominators and compensated sums"),
         "config": {"workload": (f"single LNO domain E(T): nbas={nbas} nocc={nocc[0]}/{nocc[1]} "
-                                f"naux={dom['naux']}, closed shell (aaa, aab computed; bbb, abb "
-                                f"their spin-flip images)" if args.closed_shell
+                                f"naux={dom['naux']}, closed shell" if args.closed_shell
                                 else workload_name(args.config))
-                   + (" + f_ov (RO reference)" if args.fov else ""),
+                   + (" + f_ov (RO reference)" if args.fov else "")
+                   + f"; the {K} timed steps compute the whole domain once (step s: block s "
+                     f"of {K} of every spin case's restricted triplets, all stages of the path)",
                    **cfg_public(cfg), **({"fov_sd": 0.02} if args.fov else {}),
+                   "triplets": dict(zip(CASES, ntr)),
                    "l2": f"inputs larger than L2 ({domain_bytes(nbas, nocc, dom['naux']) / 1e9:.1f} GB)",
                    "parallelism": f"replicas x{world} (one domain per GPU)"},
-        "domains_per_s": world * args.steps / (ms_max / 1e3),
-        "energy_Eh": {c: out[c] for c in CASES + ("total",)},
+        "domains_per_s": world / (ms_max / 1e3),
+        "energy_Eh": e_case,
+        "accuracy": accuracy,
         "parity": parity,
         "roofline": {"kernel": "tc_gemm_sliced (W contraction)", "bound": "tensor",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "traffic_unit": "GB per launch (ncu DRAM bytes per tensor flop, scaled)",
                      "peak_source": f"{pk['source']} bf16 sustained",
-                     "per_launch": {"ms": tc_launch_ms, "tensor_flops": tc_flops_launch}},
+                     "per_launch": {"ms": tc_launch_ms, "tensor_flops": tc_flops_launch,
+                                    "launches": nlaunch}},
         "roofline_energy": {"kernel": "energy_f32 (W/V assembly, W(W+V)/D, sums)",
                             "bound": "alu", "achieved": en_achieved, "peak": en_peak,
                             "unit": "TFLOP/s (FP32)", "frac": en_achieved / en_peak,
                             "elements": n_same + n_mixed, "passes": passes,
-                            "elements_per_s": passes * (n_same + n_mixed) / (s_last["ms_energy"] / 1e3),
+                            "elements_per_s": passes * (n_same + n_mixed) / (tot["ms_energy"] / 1e3),
                             "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock"},
-        "breakdown_ms": {k: s_last[k] for k in ("ms_total", "ms_stage", "ms_contract",
-                                                "ms_energy")},
+        "breakdown_ms": {"ms_total": tot["ms_total"], "ms_stage": tot["ms_stage"],
+                         "ms_contract": tot["ms_contract"], "ms_energy": tot["ms_energy"]},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "cpu_baseline": cpu,
         "fp64_gpu_path": fp64,
-        "e2e": None if out_e2e is None else {
-            "value": alg / e2e_s / 1e12, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": 40, "seconds_per_step": e2e_s, "energy_Eh": out_e2e["total"]},
+        "e2e": e2e,
         "gen_seconds": t_gen,
     }
     if rank == 0:
@@ -603,6 +693,49 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20,
+                    help="timed steps; together they compute the whole domain once")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c1", choices=sorted(CONFIGS) + ["custom", "c3"])
+    ap.add_argument("--c3-sample", type=int, default=8, help="domains of the c3 batch")
+    ap.add_argument("--backward", action="store_true", help="time the adjoint on a sample")
+    ap.add_argument("--bwd-sample", type=int, default=1, help="adjoint triplets per case")
+    ap.add_argument("--precision", default="bf16x10",
+                    choices=["bf16x15", "bf16x10", "bf16x6", "bf16x3"])
+    ap.add_argument("--ref-precision", default="bf16x15", choices=["bf16x15", "none"],
+                    help="whole-domain reference run that measures the domain-total error")
+    ap.add_argument("--cpu-sample", type=int, default=2, help="oracle triplets per case")
+    ap.add_argument("--cpu-seconds", type=float, default=30.0)
+    ap.add_argument("--fp64-sample", type=int, default=32, help="FP64-path triplets per case")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--closed-shell", action="store_true",
+                    help="closed-shell domain (nocc of spin up for both spins, identical data); "
+                         "both spins passed as the same arrays, so the spin-flip images run once")
+    ap.add_argument("--fov", action="store_true",
+                    help="restricted open-shell domain: add an f_ov block (and time the "
+                         "orbital contributions too)")
+    ap.add_argument("--shape", default=None,
+                    help="custom domain nbas,nalpha,nbeta,naux (recipe of the configs, seed 5)")
+    args = ap.parse_args()
+    if args.shape:
+        nbas_, na_, nb_, naux_ = (int(x) for x in args.shape.split(","))
+        CONFIGS["custom"] = dict(nbas=nbas_, nocc=(na_, nb_), naux=naux_, L=naux_ / 4.0, seed=5)
+        args.config = "custom"
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.config == "c3":
+        return run_c3(args)
+    if args.backward:
+        return run_backward(args)
+    return run_domain(args)
 
 
 if __name__ == "__main__":

@@ -15,9 +15,9 @@
  * Restricted ranges: aaa/bbb i<j<k and a<b<c; aab i<j (alpha), K (beta),
  * a<b (alpha), C (beta); abb I<J (beta), k (alpha), A<B (beta), c (alpha).
  * The four-index integrals are assembled from density-fitted three-centre
- * factors, (pq|rs) = sum_Q B^Q_pq B^Q_rs (Sec. 3.2, eqs ed_eri/ed_df_int with
+ * factors, (pq|rs) = sum_Q B^Q_pq B^Q_rs (Sec. 3.3, eqs ed_eri/ed_df_int with
  * B = I L^-T already applied), one auxiliary index shared by both spins as the
- * mixed-spin integrals require (Sec. 3.7).
+ * mixed-spin integrals require (Sec. 3.6).
  *
  * General conventions
  *  - Every function returns LNO_OT_OK (0) or a negative lno_ot_status code;
@@ -55,7 +55,7 @@ typedef enum {
   LNO_OT_EUNSUPPORTED = -6  /* option or input not supported by this build */
 } lno_ot_status;
 
-/* Arithmetic of the W contractions (Sec. 3.8 (T) step).
+/* Arithmetic of the W contractions (Sec. 3.7, the (T) step).
  *  FP64    plain float64 on the CUDA cores for everything (comparator path).
  *  BF16X3  tensor cores (tcgen05, BF16 inputs, FP32 accumulate): every
  *          float64 operand is split into 2 BF16 slices with an exact power of
@@ -66,13 +66,19 @@ typedef enum {
  *  BF16X10 4 slices per operand and 10 slice products (8 bits more again):
  *          the accurate mode for large domains, where the BF16X6 truncation
  *          adds up over ~1e5 triplets; about 1.7x the contraction time.
+ *  BF16X15 5 slices per operand and 15 slice products, with the DF assembly
+ *          on 5 slices too: 8 bits more again than BF16X10 in both steps, at
+ *          about 1.5x its contraction time.  The reference mode against which
+ *          the domain-total error of the faster modes is measured when a
+ *          float64 run of a whole domain is too slow.
  *  TF32    reserved; returns LNO_OT_EUNSUPPORTED in this build. */
 typedef enum {
   LNO_OT_FP64 = 0,
   LNO_OT_BF16X3 = 1,
   LNO_OT_TF32 = 2,
   LNO_OT_BF16X6 = 3,
-  LNO_OT_BF16X10 = 4
+  LNO_OT_BF16X10 = 4,
+  LNO_OT_BF16X15 = 5
 } lno_ot_precision;
 
 typedef struct lno_ot_ctx lno_ot_ctx; /* opaque: device, stream, workspace */
@@ -85,10 +91,12 @@ typedef struct {
   size_t workspace_bytes; /* upper bound on device workspace; 0 = no bound */
   const char* tune_cache; /* NULL, or a tuning table written by the autotuner
                              (paper_2311_10048_gb300/tune.py): text lines
-                             "vmax cluster group_cap" giving, per bucket of
-                             virtual-space size, the contraction variant
-                             (1 = 2-CTA multicast clusters) and the cap on
-                             triplets per contraction launch.  Unreadable
+                             "vmax bn group_cap" giving, per bucket of
+                             virtual-space size, the tile width of the W
+                             contraction (64, 128 or 256 where the precision
+                             has that variant; 0 = its default) and the cap
+                             on triplets per contraction launch.  Lines
+                             starting with '#' are comments.  Unreadable
                              file: lno_ot_init returns LNO_OT_EINVAL. */
 } lno_ot_options;
 
@@ -224,11 +232,24 @@ LNO_OT_API const char* lno_ot_strerror(int code);
 /* Diagnostic (no counterpart in the paper): the tensor-core contraction
  * kernel of the W step on one plain product, C[n][m] = sum_k A[m][k] B[n][k]
  * for device float64 A [M][K], B [N][K], C [N][M] (C written), with S BF16
- * slices per operand (S = 1..4; the W step uses S = 2 or 3, the DF assembly
- * S = 4).  Synchronous on `stream` (cudaStream_t, NULL = legacy default).
+ * slices per operand (S = 1..5; the W step uses S = 2..5, the DF assembly
+ * S = 4 or 5).  Synchronous on `stream` (cudaStream_t, NULL = legacy default).
  * Returns LNO_OT_EUNSUPPORTED on devices other than sm_103. */
 LNO_OT_API int lno_ot_selftest_gemm(int device, int S, int M, int N, int K, const double* A,
                                     const double* B, double* C, void* stream);
+
+/* Diagnostic (no counterpart in the paper): checks the bounded device waits
+ * of the contraction kernel.  Runs one 128 x 256 tile with the kernel's test
+ * hook that issues no copy, so its first wait for operand data can only end
+ * by the time limit `wait_cycles` (1000 .. the library's normal limit of
+ * 4e9 cycles); the kernel then records which wait gave up, releases its TMEM
+ * and returns, and the context stays usable.  Returns LNO_OT_ETIMEOUT when
+ * the bounded wait behaved as designed (*code, if not NULL, = the kernel's
+ * code of the wait that gave up: 3 MMA thread, 6 epilogue), LNO_OT_OK if no
+ * wait gave up, another status on a CUDA failure or bad argument.  Allocates
+ * its own small scratch; synchronous on `stream`. */
+LNO_OT_API int lno_ot_selftest_timeout(int device, long long wait_cycles, int* code,
+                                       void* stream);
 
 /* The same product as lno_ot_selftest_gemm (same slicing, same kernel, same
  * result) for callers that must not allocate device memory: programs whose
@@ -239,8 +260,10 @@ LNO_OT_API int lno_ot_selftest_gemm(int device, int S, int M, int N, int K, cons
  * the library.  Operands must fit: 256 B + sum over A and B of
  * S * ceil8(rows * ceil8(K)) * 2 bytes (each part rounded up to 256 B)
  * <= 64 MiB, else LNO_OT_EINVAL (lno_ot_last_error() says how much is needed).
- * The first call on a device looks up the array's address (make it before
- * any stream capture).  Every call reuses the array and clears what must
+ * A, B and C must be device (or managed) memory of `device`, else
+ * LNO_OT_EDEVICE before anything runs; the caller's current device is restored
+ * on return.  The first call on a device looks up the array's address and the
+ * device's properties (make it before any stream capture).  Every call reuses the array and clears what must
  * start at zero; calls that overlap on the GPU race on it.  Synchronous on
  * `stream` (NULL = legacy default stream). */
 LNO_OT_API int lno_ot_gemm_sliced_noalloc(int device, int S, int M, int N, int K, const double* A,

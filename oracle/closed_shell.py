@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
 arXiv 2311.10048 states that the open-shell method is identical to its
-closed-shell counterpart for closed-shell systems (Sec. 6, Summary) and that
-the NAF step reduces to the closed-shell one in that limit (Sec. 3.7).  The
+closed-shell counterpart for closed-shell systems (Sec. 8, Summary) and that
+the NAF step reduces to the closed-shell one in that limit (Sec. 3.6).  The
 closed-shell (T) energy used here is the textbook spin-adapted expression
 (the CCSD(T) reference of eq cim_pt_energy) in spatial orbitals:
 

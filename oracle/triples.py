@@ -21,7 +21,7 @@ with P(i/jk) f(ijk) = f(ijk) - f(jik) - f(kji).  This module evaluates the
 same sum one restricted occupied triplet at a time with spatial orbitals:
 same spin i<j<k with a<b<c, mixed spin i<j (spin s), K (spin t) with
 a<b (s), C (t).  Mulliken integrals come from the DF factors,
-(pq|rs) = sum_Q B^Q_pq B^Q_rs (Sec. 3.2, eq ed_df_int with B = I L^-T).
+(pq|rs) = sum_Q B^Q_pq B^Q_rs (Sec. 3.3, eq ed_df_int with B = I L^-T).
 
 The f_ia term is the restricted open-shell one: with an RO reference the
 semicanonical Fock matrix keeps an occupied-virtual block (Sec. 3.3, eq

@@ -122,6 +122,29 @@ struct TcProb {
   void* out;        // XT base of this problem (float or double), [N][ldo]
 };
 
+// Bounded-wait settings of one contraction launch: wait_cycles limits every
+// wait for work; starve = 1 is the timeout test hook (no copy is issued, so
+// the first wait for data runs out).  Library calls use tc_normal().
+struct TcDiag {
+  long long wait_cycles;
+  int starve;
+};
+
+// tc_gemm.cu: grouped sliced contraction.  mA: maps with 128-row boxes,
+// mB: maps with BN-row boxes; instances (S, BN, OutT) are listed there.
+template <int S, int BN, typename OutT>
+cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
+                           int nprob, int M, int N, int ldo, double scale, int* flag,
+                           unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag);
+long long tc_default_wait_cycles();
+inline TcDiag tc_normal() { return TcDiag{tc_default_wait_cycles(), 0}; }
+int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
+                     int64_t slice_stride, int box_rows);
+int sliced_product_bn(int S);
+cudaError_t launch_sliced_product(int S, const CUtensorMap* mA, const CUtensorMap* mB,
+                                  const TcProb* dp, int M, int N, double scale, int* flag,
+                                  int nsm, cudaStream_t st, TcDiag dg);
+
 // Operand stores used by the layout kernels.  `part` says whether the value
 // is an amplitude (0) or an integral (1): the two have separate scales.
 struct StoreF64 {

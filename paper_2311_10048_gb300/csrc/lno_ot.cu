@@ -73,18 +73,6 @@ cudaError_t launch_gather_rows(const void* src, void* dst, const int* list, int 
                                int64_t dst_slice_bytes, cudaStream_t s);
 cudaError_t launch_scatter_add_rows(const double* src, double* dst, const int* list, int nlist,
                                     int64_t row, cudaStream_t s);
-// tc_gemm.cu
-int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
-                     int64_t slice_stride, int box_rows);
-template <int S, int BN, typename OutT>
-cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
-                           int nprob, int M, int N, int ldo, double scale, int* flag,
-                           unsigned long long* amax, int nsm, cudaStream_t st);
-template <int S, int BN, typename OutT>
-cudaError_t launch_tc_gemm_mc(const CUtensorMap* mA64, const CUtensorMap* mB,
-                              const TcProb* probs_dev, int nprob, int M, int N, int ldo,
-                              double scale, int* flag, unsigned long long* amax, int nsm,
-                              cudaStream_t st);
 // backward.cu
 struct GemmS {
   const double* A;
@@ -142,11 +130,11 @@ struct lno_ot_ctx {
   bool own_stream = false;
   size_t ws_limit = 0;
   int nsm = 152;
-  bool cluster = true;                 // W contractions in 2-CTA multicast clusters
   // tuning table: per virtual-space size bucket (rows of the contraction,
-  // ascending vmax) the contraction variant and the triplet-group cap
+  // ascending vmax) the contraction tile width (0 = the precision's default)
+  // and the triplet-group cap
   struct TuneRow {
-    int vmax, cluster, group_cap;
+    int vmax, bn, group_cap;
   };
   std::vector<TuneRow> tune;
   const TuneRow* tune_for(int v) const {
@@ -236,9 +224,42 @@ struct Operand {
   __nv_bfloat16* bf = nullptr;
   int S = 0;
   int64_t slice_stride = 0;
-  CUtensorMap mapA, mapA64, mapB, mapB128;  // box rows: 128 / 64 (A role), 256 / 128 (B role)
+  CUtensorMap map128, map256, map64;  // TMA maps with boxes of 128 (A role, B of BN 128), 256, 64 rows
   int64_t total_rows() const { return (int64_t)nslot * rows; }
 };
+
+// Tile width of the W contraction for S slices: the tuned value when it is
+// one the build has (S * BN <= 512 TMEM columns), else the default.
+int contract_bn(int S, int bn) {
+  switch (S) {
+    case 2: return bn == 128 ? 128 : 256;
+    case 3: return bn == 64 ? 64 : 128;
+    case 4: return bn == 64 ? 64 : 128;
+    default: return 64;
+  }
+}
+
+const CUtensorMap& map_for(const Operand& op, int box) {
+  return box == 256 ? op.map256 : box == 64 ? op.map64 : op.map128;
+}
+
+// One grouped W-contraction launch with float32 output.
+cudaError_t launch_contract(int S, int bn_req, const Operand& A0, const Operand& A1,
+                            const Operand& B0, const Operand& B1, const TcProb* dpt, int nprob,
+                            int M, int N, int ldo, double scale, int* flag, int nsm,
+                            cudaStream_t st) {
+  const int bn = contract_bn(S, bn_req);
+  CUtensorMap mA[2] = {A0.map128, A1.map128};
+  CUtensorMap mB[2] = {map_for(B0, bn), map_for(B1, bn)};
+  const TcDiag dg = tc_normal();
+#define LNO_CALL(SS, BB) \
+  launch_tc_gemm<SS, BB, float>(mA, mB, dpt, nprob, M, N, ldo, scale, flag, nullptr, nsm, st, dg)
+  if (S == 2) return bn == 128 ? LNO_CALL(2, 128) : LNO_CALL(2, 256);
+  if (S == 3) return bn == 64 ? LNO_CALL(3, 64) : LNO_CALL(3, 128);
+  if (S == 4) return bn == 64 ? LNO_CALL(4, 64) : LNO_CALL(4, 128);
+  return LNO_CALL(5, 64);
+#undef LNO_CALL
+}
 
 struct Run {
   lno_ot_ctx* ctx;
@@ -286,14 +307,10 @@ struct Run {
     } else {
       op.slice_stride = round_up(n, 8);
       TRY(ar.get(&op.bf, (size_t)(op.slice_stride * op.S)));
-      TRY(make_operand_map(&op.mapA, op.bf, op.Kp, std::max<int64_t>(op.total_rows(), 1), op.S,
-                           op.slice_stride, 128));
-      TRY(make_operand_map(&op.mapB, op.bf, op.Kp, std::max<int64_t>(op.total_rows(), 1), op.S,
-                           op.slice_stride, 256));
-      TRY(make_operand_map(&op.mapB128, op.bf, op.Kp, std::max<int64_t>(op.total_rows(), 1),
-                           op.S, op.slice_stride, 128));
-      TRY(make_operand_map(&op.mapA64, op.bf, op.Kp, std::max<int64_t>(op.total_rows(), 1), op.S,
-                           op.slice_stride, 64));
+      const int64_t rows_ = std::max<int64_t>(op.total_rows(), 1);
+      TRY(make_operand_map(&op.map128, op.bf, op.Kp, rows_, op.S, op.slice_stride, 128));
+      TRY(make_operand_map(&op.map256, op.bf, op.Kp, rows_, op.S, op.slice_stride, 256));
+      TRY(make_operand_map(&op.map64, op.bf, op.Kp, rows_, op.S, op.slice_stride, 64));
     }
     return LNO_OT_OK;
   }
@@ -328,10 +345,17 @@ struct Run {
     TcProb* dp;
     TRY(arena.get(&dp, 1));
     CU(cudaMemcpyAsync(dp, &p, sizeof p, cudaMemcpyHostToDevice, st));
-    CUtensorMap mA[2] = {Lo.mapA, Lo.mapA}, mB[2] = {Ro.mapB128, Ro.mapB128};
     const double scale = sigB * sigB * std::ldexp(1.0, -14);
-    CU(launch_tc_gemm<4, 128, double>(mA, mB, dp, 1, M, N, ldo, scale, ctx->d_flag,
-                                      amax_pass ? ctx->d_amax : nullptr, ctx->nsm, st));
+    unsigned long long* am = amax_pass ? ctx->d_amax : nullptr;
+    if (Sdf == 5) {
+      CUtensorMap mA[2] = {Lo.map128, Lo.map128}, mB[2] = {Ro.map64, Ro.map64};
+      CU(launch_tc_gemm<5, 64, double>(mA, mB, dp, 1, M, N, ldo, scale, ctx->d_flag, am,
+                                       ctx->nsm, st, tc_normal()));
+    } else {
+      CUtensorMap mA[2] = {Lo.map128, Lo.map128}, mB[2] = {Ro.map128, Ro.map128};
+      CU(launch_tc_gemm<4, 128, double>(mA, mB, dp, 1, M, N, ldo, scale, ctx->d_flag, am,
+                                        ctx->nsm, st, tc_normal()));
+    }
     return LNO_OT_OK;
   }
 
@@ -390,6 +414,10 @@ struct Run {
         if (f64)
           CU(launch_transpose_block(dom->B[s], naux, nbas, b.p0, b.np, b.q0, b.nq, b.op->Kp,
                                     StoreF64{b.op->f64}, st));
+        else if (Sdf == 5)
+          CU(launch_transpose_block(
+              dom->B[s], naux, nbas, b.p0, b.np, b.q0, b.nq, b.op->Kp,
+              StoreSlices<5>{b.op->bf, b.op->slice_stride, 128.0 / sigB, 128.0 / sigB}, st));
         else
           CU(launch_transpose_block(
               dom->B[s], naux, nbas, b.p0, b.np, b.q0, b.nq, b.op->Kp,
@@ -503,7 +531,7 @@ struct SpinPass {
   std::vector<int> slotAT, slotBT, slotA1, slotBG, slotBF, slotAT2;  // -1 = unused
   std::vector<int2> listAT, listA1, listAT2;
   std::vector<int> listBT, listBG, listBF;
-  bool use_cluster = true;   // contraction variant of the current case
+  int bn = 0;                // contraction tile width of the current case (0 = default)
   int group_cap = 64;        // triplets per group (upper bound)
   double* t2st = nullptr;    // [os][ot][vs][vt]
   const double* t2ss = nullptr;
@@ -743,6 +771,9 @@ struct SpinPass {
     if (R.S == 4)
       return pack_all(R.slices<4>(AT), R.slices<4>(BT), R.slices<4>(A1), R.slices<4>(BG),
                       R.slices<4>(BF), R.slices<4>(AT2));
+    if (R.S == 5)
+      return pack_all(R.slices<5>(AT), R.slices<5>(BT), R.slices<5>(A1), R.slices<5>(BG),
+                      R.slices<5>(BF), R.slices<5>(AT2));
     return pack_all(R.slices<3>(AT), R.slices<3>(BT), R.slices<3>(A1), R.slices<3>(BG),
                     R.slices<3>(BF), R.slices<3>(AT2));
   }
@@ -758,32 +789,9 @@ struct SpinPass {
       CU(launch_gemm_f64(dpf, nprob, M, N, ldo, R.st));
     } else {
       CU(cudaMemcpyAsync(dpt, pt.data(), nprob * sizeof(TcProb), cudaMemcpyHostToDevice, R.st));
-      CUtensorMap mA[2] = {opA0.mapA, opA1.mapA};
-      CUtensorMap mA64[2] = {opA0.mapA64, opA1.mapA64};
-      CUtensorMap mB[2] = {R.S == 2 ? opB0.mapB : opB0.mapB128, R.S == 2 ? opB1.mapB : opB1.mapB128};
       const double scale = R.sigT * R.sigI * std::ldexp(1.0, -14);
-      int* fl = R.ctx->d_flag;
-      const int nsm = R.ctx->nsm;
-      if (use_cluster) {
-        if (R.S == 2)
-          CU(launch_tc_gemm_mc<2, 256, float>(mA64, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr,
-                                              nsm, R.st));
-        else if (R.S == 4)
-          CU(launch_tc_gemm_mc<4, 128, float>(mA64, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr,
-                                              nsm, R.st));
-        else
-          CU(launch_tc_gemm_mc<3, 128, float>(mA64, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr,
-                                              nsm, R.st));
-      } else if (R.S == 2) {
-        CU(launch_tc_gemm<2, 256, float>(mA, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr, nsm,
-                                         R.st));
-      } else if (R.S == 4) {
-        CU(launch_tc_gemm<4, 128, float>(mA, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr, nsm,
-                                         R.st));
-      } else {
-        CU(launch_tc_gemm<3, 128, float>(mA, mB, dpt, nprob, M, N, ldo, scale, fl, nullptr, nsm,
-                                         R.st));
-      }
+      CU(launch_contract(R.S, bn, opA0, opA1, opB0, opB1, dpt, nprob, M, N, ldo, scale,
+                         R.ctx->d_flag, R.ctx->nsm, R.st));
     }
     if (e1) cudaEventRecord(e1, R.st);
     if (e0 && e1) R.contract_ev.push_back({e0, e1});
@@ -816,10 +824,10 @@ struct SpinPass {
     const int P2 = (int)round_up(std::max(M2, 1), 16);
     const int64_t per_trip = (N1 * P1 + N2 * P2) * (int64_t)esz;
     const int64_t budget = (int64_t)6 << 30;
-    use_cluster = R.ctx->cluster;
+    bn = 0;
     group_cap = 64;
     if (const auto* row = R.ctx->tune_for(v)) {
-      use_cluster = row->cluster != 0;
+      bn = row->bn;
       group_cap = std::max(1, row->group_cap);
     }
     int G = (int)std::max<int64_t>(
@@ -1101,7 +1109,11 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
   ctx->ev_used = 0;
   Run R(ctx, dom);
   R.f64 = ctx->prec == LNO_OT_FP64;
-  R.S = ctx->prec == LNO_OT_BF16X6 ? 3 : ctx->prec == LNO_OT_BF16X10 ? 4 : 2;
+  R.S = ctx->prec == LNO_OT_BF16X6    ? 3
+        : ctx->prec == LNO_OT_BF16X10 ? 4
+        : ctx->prec == LNO_OT_BF16X15 ? 5
+                                      : 2;
+  R.Sdf = ctx->prec == LNO_OT_BF16X15 ? 5 : 4;
   CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
   cudaEvent_t t0 = R.event(), t1 = R.event(), t2 = R.event();
   if (t0) cudaEventRecord(t0, R.st);
@@ -1669,7 +1681,7 @@ extern "C" {
 
 int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
   if (!ctx || !opt) return LNO_OT_EINVAL;
-  if (opt->precision < 0 || opt->precision > 4) return LNO_OT_EINVAL;
+  if (opt->precision < 0 || opt->precision > LNO_OT_BF16X15) return LNO_OT_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
     cudaGetLastError();
@@ -1686,11 +1698,7 @@ int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
   c->prec = opt->precision;
   c->ws_limit = opt->workspace_bytes;
   c->nsm = prop.multiProcessorCount;
-  {  // kernel variant of the W contractions (tuning knob; default: clusters)
-    const char* ev = getenv("LNO_OT_CLUSTER");
-    c->cluster = !(ev && ev[0] == '0');
-  }
-  if (opt->tune_cache && opt->tune_cache[0]) {  // "vmax cluster group_cap" per line
+  if (opt->tune_cache && opt->tune_cache[0]) {  // "vmax bn group_cap" per line
     FILE* f = fopen(opt->tune_cache, "r");
     if (!f) {
       lno_ot_destroy(c);
@@ -1700,7 +1708,7 @@ int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
     while (fgets(line, sizeof line, f)) {
       if (line[0] == '#') continue;
       lno_ot_ctx::TuneRow r;
-      if (sscanf(line, "%d %d %d", &r.vmax, &r.cluster, &r.group_cap) == 3 && r.vmax > 0)
+      if (sscanf(line, "%d %d %d", &r.vmax, &r.bn, &r.group_cap) == 3 && r.vmax > 0)
         c->tune.push_back(r);
     }
     fclose(f);
@@ -1802,7 +1810,7 @@ const char* lno_ot_version(void) { return "lno_ot 0.1 sm_103a"; }
 
 int lno_ot_selftest_gemm(int device, int S, int M, int N, int K, const double* A, const double* B,
                          double* Cout, void* stream) {
-  if (S < 1 || S > 4 || M <= 0 || N <= 0 || K <= 0 || !A || !B || !Cout) return LNO_OT_EINVAL;
+  if (S < 1 || S > 5 || M <= 0 || N <= 0 || K <= 0 || !A || !B || !Cout) return LNO_OT_EINVAL;
   CU(cudaSetDevice(device));
   cudaDeviceProp prop;
   CU(cudaGetDeviceProperties(&prop, device));
@@ -1857,7 +1865,7 @@ int lno_ot_selftest_gemm(int device, int S, int M, int N, int K, const double* A
   CU(cudaMemcpyAsync(b16, sb16.data(), sb16.size() * 2, cudaMemcpyHostToDevice, st));
   CUtensorMap mA[2], mB[2];
   TRY(make_operand_map(&mA[0], a16, Kp, M, S, na, 128));
-  TRY(make_operand_map(&mB[0], b16, Kp, N, S, nb, S <= 2 ? 256 : 128));
+  TRY(make_operand_map(&mB[0], b16, Kp, N, S, nb, sliced_product_bn(S)));
   mA[1] = mA[0];
   mB[1] = mB[0];
   TcProb p{};
@@ -1868,16 +1876,52 @@ int lno_ot_selftest_gemm(int device, int S, int M, int N, int K, const double* A
   TRY(ar.get(&dp, 1));
   CU(cudaMemcpyAsync(dp, &p, sizeof p, cudaMemcpyHostToDevice, st));
   const double scale = sa * sb * std::ldexp(1.0, -14);
-  int nsm = prop.multiProcessorCount;
-  switch (S) {
-    case 1: CU(launch_tc_gemm<1, 256, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st)); break;
-    case 2: CU(launch_tc_gemm<2, 256, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st)); break;
-    case 3: CU(launch_tc_gemm<3, 128, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st)); break;
-    default: CU(launch_tc_gemm<4, 128, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st));
-  }
+  CU(launch_sliced_product(S, mA, mB, dp, M, N, scale, flag, prop.multiProcessorCount, st,
+                           tc_normal()));
   int hflag = 0;
   CU(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
+  return hflag ? LNO_OT_ETIMEOUT : LNO_OT_OK;
+}
+
+int lno_ot_selftest_timeout(int device, long long wait_cycles, int* code, void* stream) {
+  if (wait_cycles < 1000 || wait_cycles > tc_default_wait_cycles()) return LNO_OT_EINVAL;
+  if (code) *code = 0;
+  CU(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  CU(cudaGetDeviceProperties(&prop, device));
+  if (!(prop.major == 10 && prop.minor == 3)) return LNO_OT_EUNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // one 128 x 256 tile of a 2-slice product, K = 64: grid of one CTA
+  constexpr int S = 2, M = 128, N = 256, K = 64;
+  Arena ar(st, 0);
+  int* flag;
+  __nv_bfloat16 *a16, *b16;
+  double* out;
+  TcProb* dp;
+  TRY(ar.get(&flag, 1));
+  TRY(ar.get(&a16, (size_t)S * M * K));
+  TRY(ar.get(&b16, (size_t)S * N * K));
+  TRY(ar.get(&out, (size_t)M * N));
+  TRY(ar.get(&dp, 1));
+  CU(cudaMemsetAsync(flag, 0, 4, st));
+  CU(cudaMemsetAsync(a16, 0, (size_t)S * M * K * 2, st));
+  CU(cudaMemsetAsync(b16, 0, (size_t)S * N * K * 2, st));
+  CUtensorMap mA[2], mB[2];
+  TRY(make_operand_map(&mA[0], a16, K, M, S, (int64_t)M * K, 128));
+  TRY(make_operand_map(&mB[0], b16, K, N, S, (int64_t)N * K, sliced_product_bn(S)));
+  mA[1] = mA[0];
+  mB[1] = mB[0];
+  TcProb p{};
+  p.nseg = 1;
+  p.seg[0] = TcSeg{0, 0, 0, 0, K, 0};
+  p.out = out;
+  CU(cudaMemcpyAsync(dp, &p, sizeof p, cudaMemcpyHostToDevice, st));
+  CU(launch_sliced_product(S, mA, mB, dp, M, N, 1.0, flag, 1, st, TcDiag{wait_cycles, 1}));
+  int hflag = 0;
+  CU(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (code) *code = hflag;
   return hflag ? LNO_OT_ETIMEOUT : LNO_OT_OK;
 }
 

@@ -11,11 +11,16 @@
 // kScratchBytes, which every GPU that loads the library holds until exit.
 //
 // Set-up: the first call on a device (with that device current) looks up the
-// array's device address with cudaGetSymbolAddress and caches it; make that
-// first call before any stream capture.  Every call shares the array and
-// leaves its contents behind: the reduction and the flag are cleared at the
-// start of each call, and two calls whose work overlaps on the GPU (different
-// streams, or different host threads) race on it.
+// array's device address with cudaGetSymbolAddress and the device's SM count
+// and compute capability, and caches them; make that first call before any
+// stream capture.  Every call shares the array and leaves its contents
+// behind: the reduction and the flag are cleared at the start of each call,
+// and two calls whose work overlaps on the GPU (different streams, or
+// different host threads) race on it.
+//
+// Arguments are checked before anything is launched: A, B and C must be
+// device (or managed) memory of `device` (else LNO_OT_EDEVICE), and the
+// caller's current device is restored on every return.
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -24,12 +29,6 @@
 
 namespace lno {
 cudaError_t launch_absmax(const double*, int64_t, unsigned long long*, cudaStream_t);
-int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
-                     int64_t slice_stride, int box_rows);
-template <int S, int BN, typename OutT>
-cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
-                           int nprob, int M, int N, int ldo, double scale, int* flag,
-                           unsigned long long* amax, int nsm, cudaStream_t st);
 }  // namespace lno
 
 using namespace lno;
@@ -42,25 +41,65 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
+// Per-device set-up, done once with the device current.
+struct DeviceSetup {
+  void* scratch = nullptr;  // device address of g_scratch
+  int nsm = 0;
+  int cc = 0;               // 10 * major + minor
+};
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+DeviceSetup g_setup[kMaxDevices];
 
-// Device address of g_scratch on `device` (which must be current).
-int scratch_address(int device, unsigned char** out) {
+int device_setup(int device, DeviceSetup* out) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[device]) {
+  DeviceSetup& d = g_setup[device];
+  if (!d.scratch) {
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+      lno_set_last_error("cudaGetDeviceProperties", e, __FILE__, __LINE__);
+      cudaGetLastError();
+      return LNO_OT_ECUDA;
+    }
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess || p == nullptr) {
       lno_set_last_error("cudaGetSymbolAddress(g_scratch)", e, __FILE__, __LINE__);
       cudaGetLastError();
       return LNO_OT_ECUDA;
     }
-    g_scratch_ptr[device] = p;
+    d.nsm = prop.multiProcessorCount;
+    d.cc = 10 * prop.major + prop.minor;
+    d.scratch = p;
   }
-  *out = static_cast<unsigned char*>(g_scratch_ptr[device]);
+  *out = d;
   return LNO_OT_OK;
 }
+
+// LNO_OT_OK if p is device or managed memory of `device`.
+int check_device_ptr(const void* p, int device) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return LNO_OT_EDEVICE;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return LNO_OT_EDEVICE;
+  return at.device == device ? LNO_OT_OK : LNO_OT_EDEVICE;
+}
+
+// Restores the caller's current device when the call returns.
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 // rows x K float64 (row-major) -> S BF16 slices [s][row][Kp], zero for k >= K.
 template <int S>
@@ -123,15 +162,22 @@ extern "C" LNO_OT_API int lno_ot_gemm_sliced_noalloc(int device, int S, int M, i
     lno_set_last_error(msg, cudaSuccess, __FILE__, __LINE__);
     return LNO_OT_EINVAL;
   }
+  int ndev = 0;
+  NA_CU(cudaGetDeviceCount(&ndev));
+  if (device >= ndev) return LNO_OT_EDEVICE;
+  DeviceGuard guard;
   NA_CU(cudaSetDevice(device));
-  cudaDeviceProp prop;
-  NA_CU(cudaGetDeviceProperties(&prop, device));
-  if (!(prop.major == 10 && prop.minor == 3)) return LNO_OT_EUNSUPPORTED;
-  unsigned char* base = nullptr;
-  {
-    const int rc = scratch_address(device, &base);
+  for (const void* p : {(const void*)A, (const void*)B, (const void*)Cout}) {
+    const int rc = check_device_ptr(p, device);
     if (rc != LNO_OT_OK) return rc;
   }
+  DeviceSetup ds;
+  {
+    const int rc = device_setup(device, &ds);
+    if (rc != LNO_OT_OK) return rc;
+  }
+  if (ds.cc != 103) return LNO_OT_EUNSUPPORTED;
+  unsigned char* base = static_cast<unsigned char*>(ds.scratch);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned long long* amax = reinterpret_cast<unsigned long long*>(base);
   int* flag = reinterpret_cast<int*>(base + 16);
@@ -170,7 +216,7 @@ extern "C" LNO_OT_API int lno_ot_gemm_sliced_noalloc(int device, int S, int M, i
   }
   CUtensorMap mA[2], mB[2];
   int rc = make_operand_map(&mA[0], a16, Kp, M, S, sa, 128);
-  if (rc == LNO_OT_OK) rc = make_operand_map(&mB[0], b16, Kp, N, S, sb, S <= 2 ? 256 : 128);
+  if (rc == LNO_OT_OK) rc = make_operand_map(&mB[0], b16, Kp, N, S, sb, sliced_product_bn(S));
   if (rc != LNO_OT_OK) return rc;
   mA[1] = mA[0];
   mB[1] = mB[0];
@@ -180,13 +226,7 @@ extern "C" LNO_OT_API int lno_ot_gemm_sliced_noalloc(int device, int S, int M, i
   p.out = Cout;
   NA_CU(cudaMemcpyAsync(desc, &p, sizeof p, cudaMemcpyHostToDevice, st));
   const double scale = sca * scb * std::ldexp(1.0, -14);
-  const int nsm = prop.multiProcessorCount;
-  switch (S) {
-    case 1: NA_CU(launch_tc_gemm<1, 256, double>(mA, mB, desc, 1, M, N, M, scale, flag, nullptr, nsm, st)); break;
-    case 2: NA_CU(launch_tc_gemm<2, 256, double>(mA, mB, desc, 1, M, N, M, scale, flag, nullptr, nsm, st)); break;
-    case 3: NA_CU(launch_tc_gemm<3, 128, double>(mA, mB, desc, 1, M, N, M, scale, flag, nullptr, nsm, st)); break;
-    default: NA_CU(launch_tc_gemm<4, 128, double>(mA, mB, desc, 1, M, N, M, scale, flag, nullptr, nsm, st));
-  }
+  NA_CU(launch_sliced_product(S, mA, mB, desc, M, N, scale, flag, ds.nsm, st, tc_normal()));
   int hflag = 0;
   NA_CU(cudaMemcpyAsync(&hflag, flag, sizeof hflag, cudaMemcpyDeviceToHost, st));
   NA_CU(cudaStreamSynchronize(st));

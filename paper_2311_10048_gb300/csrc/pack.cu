@@ -418,6 +418,7 @@ LNO_INST(StoreF64)
 LNO_INST(StoreSlices<2>)
 LNO_INST(StoreSlices<3>)
 LNO_INST(StoreSlices<4>)
+LNO_INST(StoreSlices<5>)
 #undef LNO_INST
 
 }  // namespace lno

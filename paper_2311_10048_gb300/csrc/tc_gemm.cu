@@ -30,11 +30,14 @@
 // Kernel structure (one CTA per SM, persistent over tiles of 128 x BN):
 //   warp 0      TMA producer (one thread), STAGES-deep smem ring
 //   warp 1      TMEM allocator and MMA issuer (one thread); S accumulators
-//               of 128 x BN FP32 (BN = 256 for S <= 2, 128 for S >= 3; S = 4
-//               fills the 512 TMEM columns, so its epilogue is not overlapped)
+//               of 128 x BN FP32 (S * BN <= 512 TMEM columns: BN = 256 or 128
+//               for S = 2, 128 or 64 for S = 3, 4, and 64 for S = 5)
 //   warps 2..5  epilogue: tcgen05.ld -> scale -> coalesced stores along m; when
-//               TMEM has room (S = 3, BN = 128) the combined tile is parked in
+//               TMEM has room ((S + 1) BN <= 512) the combined tile is parked in
 //               spare columns so the next tile's MMAs overlap the stores
+// Tiles are visited m fastest: the CTAs that run at the same time share the
+// B tile of one n-tile (read from HBM once, the other m-tiles hit L2), and the
+// small A operand of a problem stays resident in L2.
 // Every mbarrier wait is bounded; on a timeout the kernel records an error
 // code, drains its own TMA copies and MMAs, frees TMEM and returns.
 #include "common.cuh"
@@ -75,16 +78,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Wait for phase `parity` of `bar`; false if another role raised the error
-// flag (abortable) or the time limit passed (then records `code`).
+// flag (abortable) or `limit` cycles passed (then records `code`).  Waits for
+// work use the launch's limit; the drain waits before TMEM and shared memory
+// are released always use the long kWaitCycles.
 __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* flag, int code,
-                                       bool abortable) {
+                                       bool abortable, long long limit = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 0) {
       if (abortable && *(volatile int*)flag != 0) return false;
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > limit) {
         atomicCAS(flag, 0, code);
         return false;
       }
@@ -99,28 +104,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
-}
-
-// Multicast: the box lands at the same CTA-relative offset in every CTA of
-// `mask`, and completes bytes on the barrier at the same offset in each.
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                               int c0, int c1, int c2, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -143,14 +126,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(bar),
-      "h"(mask)
       : "memory");
 }
 
@@ -207,18 +182,19 @@ struct Cfg {
   static_assert(S * BN <= 512, "one TMEM accumulator per weight class");
 };
 
-// MC = 1: one CTA per tile.  MC = 2: clusters of two CTAs on adjacent
-// n-tiles of the same m-tile; each loads half of the shared A tile and
-// multicasts it to both (A traffic from L2 halves), and each MMA commit frees
-// the stage in both CTAs (empty barriers count two arrivals).
-template <int S, int BN, typename OutT, int MC>
+// One CTA per SM, persistent over the (problem, n-tile, m-tile) units.
+// `diag` is the bounded-wait test hook: wait_cycles limits every wait for work
+// (kWaitCycles in normal launches); starve = 1 makes the producer issue no copy
+// at all, so the MMA thread's first wait (on a full barrier nothing will
+// complete) runs out after wait_cycles and the kernel takes its error exit
+// with nothing in flight.  Library calls always pass {kWaitCycles, 0}.
+template <int S, int BN, typename OutT>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
                const TcProb* __restrict__ probs, int nprob, int M, int N, int ldo, double scale,
-               int* __restrict__ flag, unsigned long long* __restrict__ amax) {
+               int* __restrict__ flag, unsigned long long* __restrict__ amax, TcDiag diag) {
   using C = Cfg<S, BN>;
-  static_assert(MC == 1 || MC == 2, "cluster of one or two CTAs");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -227,13 +203,9 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 3);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = MC == 2 ? cluster_rank() : 0u;
-  const int cid = MC == 2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-  const int ncl = MC == 2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   const int nM = (M + BM - 1) / BM, nN = (N + BN - 1) / BN;
-  const int nNu = (nN + MC - 1) / MC;            // n-tile units (pairs when MC = 2)
-  const long long nunits = (long long)nprob * nM * nNu;
-  const uint16_t mask = (uint16_t)((1u << MC) - 1u);
+  const long long nunits = (long long)nprob * nM * nN;
+  const long long wlim = diag.wait_cycles;
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + C::kStages + s); };
   const uint32_t tfull = smem_u32(bars + 2 * C::kStages);
@@ -243,18 +215,18 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
   auto b_addr = [&](int st, int sl) {
     return smem_u32(smem + st * C::kStage + S * C::kABytes + sl * C::kBBytes);
   };
-  // unit -> (problem, m-tile, n-tile of this CTA)
+  // unit -> (problem, m-tile, n-tile), m fastest
   auto decode = [&](long long u, int& mt, int& nt, long long& pr) {
     mt = (int)(u % nM);
     const long long r = u / nM;
-    nt = (int)(r % nNu) * MC + (int)rank;
-    pr = r / nNu;
+    nt = (int)(r % nN);
+    pr = r / nN;
   };
 
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), MC);
+      mbar_init(empty_bar(s), 1);
     }
     mbar_init(tfull, 1);
     mbar_init(tempty, 128);
@@ -270,7 +242,6 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (MC == 2) cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -280,8 +251,8 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
       int stage = 0;
       uint32_t phase = 0;
       uint32_t issued_mask = 0, last_phase = 0;
-      bool ok = true;
-      for (long long u = cid; u < nunits && ok; u += ncl) {
+      bool ok = diag.starve == 0;
+      for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         int mt, nt;
         long long pr;
         decode(u, mt, nt, pr);
@@ -291,20 +262,14 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
           const CUtensorMap* ma = seg.amap ? &mapA1 : &mapA0;
           const CUtensorMap* mb = seg.bmap ? &mapB1 : &mapB0;
           for (int k0 = 0; k0 < seg.K; k0 += BK) {
-            if (!mbar_wait(empty_bar(stage), phase ^ 1u, flag, 1, true)) {
+            if (!mbar_wait(empty_bar(stage), phase ^ 1u, flag, 1, true, wlim)) {
               ok = false;
               break;
             }
             mbar_expect_tx(full_bar(stage), (uint32_t)C::kStage);
 #pragma unroll
-            for (int sl = 0; sl < S; ++sl) {
-              if constexpr (MC == 1) {
-                tma_load_3d(a_addr(stage, sl), ma, full_bar(stage), k0, seg.a_row + mt * BM, sl);
-              } else {  // my half of the A rows, to both CTAs
-                tma_load_3d_mc(a_addr(stage, sl) + rank * (C::kABytes / 2), ma, full_bar(stage), k0,
-                               seg.a_row + mt * BM + (int)rank * (BM / 2), sl, mask);
-              }
-            }
+            for (int sl = 0; sl < S; ++sl)
+              tma_load_3d(a_addr(stage, sl), ma, full_bar(stage), k0, seg.a_row + mt * BM, sl);
 #pragma unroll
             for (int sl = 0; sl < S; ++sl)
               tma_load_3d(b_addr(stage, sl), mb, full_bar(stage), k0, seg.b_row + nt * BN, sl);
@@ -320,12 +285,6 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
       // every copy this thread issued must have landed before smem goes away
       for (int s = 0; s < C::kStages; ++s)
         if (issued_mask & (1u << s)) mbar_wait(full_bar(s), (last_phase >> s) & 1u, flag, 4, false);
-      if constexpr (MC == 2) {
-        // and every MMA commit of either CTA aimed at this CTA's barriers has arrived
-        for (int s = 0; s < C::kStages; ++s)
-          if (issued_mask & (1u << s))
-            mbar_wait(empty_bar(s), (last_phase >> s) & 1u, flag, 7, false);
-      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -333,12 +292,12 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
       int stage = 0;
       uint32_t phase = 0, tile_it = 0;
       bool ok = true, any = false;
-      for (long long u = cid; u < nunits && ok; u += ncl, ++tile_it) {
+      for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++tile_it) {
         int mt, nt;
         long long pr;
         decode(u, mt, nt, pr);
         const TcProb& P = probs[pr];
-        if (tile_it > 0 && !mbar_wait(tempty, (tile_it - 1) & 1u, flag, 2, true)) {
+        if (tile_it > 0 && !mbar_wait(tempty, (tile_it - 1) & 1u, flag, 2, true, wlim)) {
           ok = false;
           break;
         }
@@ -348,7 +307,7 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
           const TcSeg seg = P.seg[sg];
           const uint32_t idesc = idesc_bf16<BN>(seg.neg);
           for (int k0 = 0; k0 < seg.K; k0 += BK) {
-            if (!mbar_wait(full_bar(stage), phase, flag, 3, true)) {
+            if (!mbar_wait(full_bar(stage), phase, flag, 3, true, wlim)) {
               ok = false;
               break;
             }
@@ -370,10 +329,7 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                 }
               }
             }
-            if constexpr (MC == 1)
-              umma_commit(empty_bar(stage));
-            else
-              umma_commit_mc(empty_bar(stage), mask);
+            umma_commit(empty_bar(stage));
             if (++stage == C::kStages) {
               stage = 0;
               phase ^= 1u;
@@ -395,12 +351,12 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     float lmax = 0.f;
     // scale = sigma_A sigma_B 2^-14 is a power of two: exact in float
     const float fscale = (float)scale;
-    for (long long u = cid; u < nunits; u += ncl, ++tile_it) {
+    for (long long u = blockIdx.x; u < nunits; u += gridDim.x, ++tile_it) {
       int mt, nt;
       long long pr;
       decode(u, mt, nt, pr);
       const TcProb& P = probs[pr];
-      if (!mbar_wait(tfull, tile_it & 1u, flag, 6, true)) break;
+      if (!mbar_wait(tfull, tile_it & 1u, flag, 6, true, wlim)) break;
       tc_fence_after();
       const int m = mt * BM + row;
       OutT* out = reinterpret_cast<OutT*>(P.out);
@@ -485,7 +441,6 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
                  : "memory");
   }
-  if constexpr (MC == 2) cluster_sync();  // neither CTA leaves while the other may still signal it
 }
 
 }  // namespace
@@ -526,99 +481,63 @@ int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t row
   return r == CUDA_SUCCESS ? LNO_OT_OK : LNO_OT_ECUDA;
 }
 
+// mB must be maps with boxes of BN rows; mA boxes of 128 rows.
 template <int S, int BN, typename OutT>
 cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
                            int nprob, int M, int N, int ldo, double scale, int* flag,
-                           unsigned long long* amax, int nsm, cudaStream_t st) {
+                           unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag) {
   using C = Cfg<S, BN>;
   if (nprob <= 0 || M <= 0 || N <= 0) return cudaSuccess;
-  auto k = tc_gemm_sliced<S, BN, OutT, 1>;
+  auto k = tc_gemm_sliced<S, BN, OutT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   if (e != cudaSuccess) return e;
   const long long ntiles = (long long)nprob * ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int grid = (int)(ntiles < nsm ? ntiles : nsm);
   k<<<grid, 192, C::kSmem, st>>>(mA[0], mA[1], mB[0], mB[1], probs_dev, nprob, M, N, ldo, scale,
-                                 flag, amax);
-  return cudaGetLastError();
-}
-
-// Clusters of two CTAs sharing the A tile by TMA multicast.  The A maps must
-// have boxes of 64 rows (half a tile).
-template <int S, int BN, typename OutT>
-cudaError_t launch_tc_gemm_mc(const CUtensorMap* mA64, const CUtensorMap* mB,
-                              const TcProb* probs_dev, int nprob, int M, int N, int ldo,
-                              double scale, int* flag, unsigned long long* amax, int nsm,
-                              cudaStream_t st) {
-  using C = Cfg<S, BN>;
-  if (nprob <= 0 || M <= 0 || N <= 0) return cudaSuccess;
-  auto k = tc_gemm_sliced<S, BN, OutT, 2>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(192, 1, 1);
-  cfg.dynamicSmemBytes = C::kSmem;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  static int max_clusters = 0;
-  if (max_clusters == 0) {
-    cfg.gridDim = dim3(2 * (nsm / 2), 1, 1);
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess || n <= 0) {
-      cudaGetLastError();
-      n = nsm / 2;
-    }
-    max_clusters = n;
-  }
-  const long long nunits = (long long)nprob * ((M + BM - 1) / BM) * (((N + BN - 1) / BN + 1) / 2);
-  const int ncl = (int)(nunits < max_clusters ? nunits : max_clusters);
-  cfg.gridDim = dim3(2 * ncl, 1, 1);
-  e = cudaLaunchKernelEx(&cfg, k, mA64[0], mA64[1], mB[0], mB[1], probs_dev, nprob, M, N, ldo,
-                         scale, flag, amax);
-  if (e != cudaSuccess) return e;
+                                 flag, amax, diag);
   return cudaGetLastError();
 }
 
 int tc_products(int S) { return S * (S + 1) / 2; }
 
-template cudaError_t launch_tc_gemm_mc<2, 256, float>(const CUtensorMap*, const CUtensorMap*,
-                                                      const TcProb*, int, int, int, int, double,
-                                                      int*, unsigned long long*, int, cudaStream_t);
-template cudaError_t launch_tc_gemm_mc<3, 128, float>(const CUtensorMap*, const CUtensorMap*,
-                                                      const TcProb*, int, int, int, int, double,
-                                                      int*, unsigned long long*, int, cudaStream_t);
-template cudaError_t launch_tc_gemm_mc<4, 128, float>(const CUtensorMap*, const CUtensorMap*,
-                                                      const TcProb*, int, int, int, int, double,
-                                                      int*, unsigned long long*, int, cudaStream_t);
-template cudaError_t launch_tc_gemm<4, 128, float>(const CUtensorMap*, const CUtensorMap*,
-                                                   const TcProb*, int, int, int, int, double, int*,
-                                                   unsigned long long*, int, cudaStream_t);
+// Tile width of the single-product diagnostics for S slices.
+int sliced_product_bn(int S) { return S <= 2 ? 256 : S <= 4 ? 128 : 64; }
 
-template cudaError_t launch_tc_gemm<2, 256, float>(const CUtensorMap*, const CUtensorMap*,
-                                                   const TcProb*, int, int, int, int, double, int*,
-                                                   unsigned long long*, int, cudaStream_t);
-template cudaError_t launch_tc_gemm<3, 128, float>(const CUtensorMap*, const CUtensorMap*,
-                                                   const TcProb*, int, int, int, int, double, int*,
-                                                   unsigned long long*, int, cudaStream_t);
-template cudaError_t launch_tc_gemm<4, 128, double>(const CUtensorMap*, const CUtensorMap*,
-                                                    const TcProb*, int, int, int, int, double,
-                                                    int*, unsigned long long*, int, cudaStream_t);
-template cudaError_t launch_tc_gemm<1, 256, double>(const CUtensorMap*, const CUtensorMap*,
-                                                    const TcProb*, int, int, int, int, double,
-                                                    int*, unsigned long long*, int, cudaStream_t);
-template cudaError_t launch_tc_gemm<2, 256, double>(const CUtensorMap*, const CUtensorMap*,
-                                                    const TcProb*, int, int, int, int, double,
-                                                    int*, unsigned long long*, int, cudaStream_t);
-template cudaError_t launch_tc_gemm<3, 128, double>(const CUtensorMap*, const CUtensorMap*,
-                                                    const TcProb*, int, int, int, int, double,
-                                                    int*, unsigned long long*, int, cudaStream_t);
-template cudaError_t launch_tc_gemm<1, 256, float>(const CUtensorMap*, const CUtensorMap*,
-                                                   const TcProb*, int, int, int, int, double, int*,
-                                                   unsigned long long*, int, cudaStream_t);
+// One plain product C[n][m] = sum_k A[m][k] B[n][k] (float64 output) on
+// sliced operands already in device memory; mB boxes of sliced_product_bn(S) rows.
+cudaError_t launch_sliced_product(int S, const CUtensorMap* mA, const CUtensorMap* mB,
+                                  const TcProb* dp, int M, int N, double scale, int* flag,
+                                  int nsm, cudaStream_t st, TcDiag dg) {
+  switch (S) {
+    case 1: return launch_tc_gemm<1, 256, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    case 2: return launch_tc_gemm<2, 256, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    case 3: return launch_tc_gemm<3, 128, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    case 4: return launch_tc_gemm<4, 128, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    case 5: return launch_tc_gemm<5, 64, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    default: return cudaErrorInvalidValue;
+  }
+}
+long long tc_default_wait_cycles() { return kWaitCycles; }
+
+#define LNO_TC_INST(S, BN, T)                                                                    \
+  template cudaError_t launch_tc_gemm<S, BN, T>(const CUtensorMap*, const CUtensorMap*,          \
+                                                const TcProb*, int, int, int, int, double, int*, \
+                                                unsigned long long*, int, cudaStream_t, TcDiag);
+// W contractions (float32 output): slices x tile width
+LNO_TC_INST(2, 256, float)
+LNO_TC_INST(2, 128, float)
+LNO_TC_INST(3, 128, float)
+LNO_TC_INST(3, 64, float)
+LNO_TC_INST(4, 128, float)
+LNO_TC_INST(4, 64, float)
+LNO_TC_INST(5, 64, float)
+LNO_TC_INST(1, 256, float)
+// DF assembly and the diagnostics (float64 output)
+LNO_TC_INST(1, 256, double)
+LNO_TC_INST(2, 256, double)
+LNO_TC_INST(3, 128, double)
+LNO_TC_INST(4, 128, double)
+LNO_TC_INST(5, 64, double)
+#undef LNO_TC_INST
 
 }  // namespace lno

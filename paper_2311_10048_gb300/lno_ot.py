@@ -16,9 +16,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblno_ot.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "lno_ot.h")
 
 OK, EINVAL, EDEVICE, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-FP64, BF16X3, TF32, BF16X6, BF16X10 = 0, 1, 2, 3, 4
+FP64, BF16X3, TF32, BF16X6, BF16X10, BF16X15 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": FP64, "bf16x3": BF16X3, "tf32": TF32, "bf16x6": BF16X6,
-              "bf16x10": BF16X10}
+              "bf16x10": BF16X10, "bf16x15": BF16X15}
 CASES = ("aaa", "aab", "abb", "bbb")
 
 
@@ -97,6 +97,11 @@ def load_library(build_if_missing=False):
     lib.lno_ot_version.restype = C.c_char_p
     lib.lno_ot_last_error.argtypes = []
     lib.lno_ot_last_error.restype = C.c_char_p
+    lib.lno_ot_selftest_gemm.argtypes = [C.c_int] * 5 + [C.c_void_p] * 4
+    lib.lno_ot_selftest_gemm.restype = C.c_int
+    lib.lno_ot_selftest_timeout.argtypes = [C.c_int, C.c_longlong, C.POINTER(C.c_int),
+                                            C.c_void_p]
+    lib.lno_ot_selftest_timeout.restype = C.c_int
     _lib = lib
     return lib
 
@@ -157,9 +162,12 @@ def make_domain_struct(dom, e_trip=None, trip_sel=None, e_orb=None):
         if trip_sel is not None and trip_sel[c] is not None:
             import numpy as np
             a = np.ascontiguousarray(trip_sel[c], dtype=np.int64)
+            n = a.size
+            if n == 0:   # an empty selection still needs a non-NULL pointer
+                a = np.zeros(1, dtype=np.int64)
             keep.append(a)
             d.trip_sel[c] = a.ctypes.data
-            d.n_sel[c] = a.size
+            d.n_sel[c] = n
     return d, keep
 
 

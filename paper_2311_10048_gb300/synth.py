@@ -4,10 +4,10 @@ This module only builds inputs. It holds none of the (T) arithmetic, and both
 the GPU path (through its callers) and the CPU oracle receive its arrays as
 plain data.
 
-What a domain is (arXiv 2311.10048, Sec. 3.8 "Correlation energy calculation
+What a domain is (arXiv 2311.10048, Sec. 3.7 "Correlation energy calculation
 in the LIS"): semicanonical spin-up / spin-down orbitals of one local
 interacting subspace, DF three-centre integrals B^Q_pq with one auxiliary index
-shared by both spins (Sec. 3.7, NAF paragraph), orbital energies, and CCSD
+shared by both spins (Sec. 3.6, NAF paragraph), orbital energies, and CCSD
 T1/T2 amplitudes.  Real amplitudes come from an iterative CCSD solver; here T2
 is MP2-like, built from the same B and orbital energies, so that the sizes,
 signs and value distributions are those of a real LIS.

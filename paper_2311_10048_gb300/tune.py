@@ -2,9 +2,9 @@
 
 For each bucket it builds one synthetic domain of that virtual size (few
 occupied orbitals, so a trial takes milliseconds), times lno_ot_energy with
-every candidate row (contraction variant x triplet-group cap) written to a
+every candidate row (contraction tile width x triplet-group cap) written to a
 one-row table, and keeps the fastest.  The result is the text table the
-library reads through lno_ot_options.tune_cache ("vmax cluster group_cap").
+library reads through lno_ot_options.tune_cache ("vmax bn group_cap").
 
     python -m paper_2311_10048_gb300.tune out.txt [--precision bf16x6]
 """
@@ -16,7 +16,14 @@ import tempfile
 import time
 
 BUCKETS = (96, 160, 224, 320, 448)          # vmax of each bucket
-CANDIDATES = [(c, g) for c in (0, 1) for g in (16, 64)]
+# contraction tile widths the library has per precision (S * BN <= 512 TMEM columns)
+TILE_WIDTHS = {"bf16x3": (256, 128), "bf16x6": (128, 64), "bf16x10": (128, 64),
+               "bf16x15": (64,)}
+GROUP_CAPS = (16, 64)
+
+
+def candidates(precision):
+    return [(bn, g) for bn in TILE_WIDTHS.get(precision, (0,)) for g in GROUP_CAPS]
 
 
 def _time_row(lno_ot, dd, precision, row, reps=2):
@@ -47,14 +54,14 @@ def autotune(path, precision="bf16x6", buckets=BUCKETS, nocc=(10, 8), log=print)
         d = make_domain(v + nocc[0], nocc, naux=3 * (v + nocc[0]), L=0.75 * (v + nocc[0]),
                         seed=vmax)
         dd = lno_ot.to_device(d)
-        times = {row: _time_row(lno_ot, dd, precision, row) for row in CANDIDATES}
+        times = {row: _time_row(lno_ot, dd, precision, row) for row in candidates(precision)}
         best = min(times, key=times.get)
         rows.append((vmax,) + best)
-        log(f"bucket v<={vmax}: " + ", ".join(f"cluster={c} cap={g}: {t:.2f} ms"
+        log(f"bucket v<={vmax}: " + ", ".join(f"bn={c} cap={g}: {t:.2f} ms"
                                             for (c, g), t in times.items()) + f" -> {best}")
         del dd
     with open(path, "w") as f:
-        f.write(f"# lno_ot tuning table ({precision}); vmax cluster group_cap\n")
+        f.write(f"# lno_ot tuning table ({precision}); vmax bn group_cap\n")
         for r in rows:
             f.write(f"{r[0]} {r[1]} {r[2]}\n")
     return rows

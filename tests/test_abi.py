@@ -84,7 +84,8 @@ def test_enum_values_match_binding():
             "LNO_OT_ECUDA": lno_ot.ECUDA, "LNO_OT_ETIMEOUT": lno_ot.ETIMEOUT,
             "LNO_OT_EUNSUPPORTED": lno_ot.EUNSUPPORTED, "LNO_OT_FP64": lno_ot.FP64,
             "LNO_OT_BF16X3": lno_ot.BF16X3, "LNO_OT_TF32": lno_ot.TF32,
-            "LNO_OT_BF16X6": lno_ot.BF16X6, "LNO_OT_BF16X10": lno_ot.BF16X10}
+            "LNO_OT_BF16X6": lno_ot.BF16X6, "LNO_OT_BF16X10": lno_ot.BF16X10,
+            "LNO_OT_BF16X15": lno_ot.BF16X15}
     for k, v in want.items():
         assert enums.get(k) == v, (k, enums.get(k), v)
-    assert set(lno_ot.PRECISIONS.values()) == {0, 1, 2, 3, 4}
+    assert set(lno_ot.PRECISIONS.values()) == {0, 1, 2, 3, 4, 5}

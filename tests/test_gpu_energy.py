@@ -206,7 +206,7 @@ def test_batched_reports_per_domain_errors(lib):
 def test_tuning_table_is_read(lib, tmp_path):
     d = lno_ot.to_device(make_domain(40, (6, 4), naux=80, L=20.0, seed=1))
     ref = None
-    for rows in ("1000 0 4\n", "1000 1 64\n", "# comment\n20 0 1\n1000 1 2\n"):
+    for rows in ("1000 0 4\n", "1000 64 64\n", "# comment\n20 64 1\n1000 0 2\n"):
         p = tmp_path / "t.txt"
         p.write_text(rows)
         ctx = lno_ot.Context(0, "bf16x6", tune_cache=str(p))
@@ -250,3 +250,49 @@ def test_shapes_bf16x10_vs_oracle(ctx10, shape):
     ref = T.energy(d)
     for c in CASES:
         assert abs(out[c] - ref[c]) <= 1e-9 + 1e-9 * abs(ref[c]), c
+
+
+@pytest.mark.parametrize("prec,widths", [("bf16x3", (256, 128)), ("bf16x6", (128, 64)),
+                                         ("bf16x10", (128, 64))])
+def test_tile_widths_give_bitwise_equal_results(lib, tmp_path, prec, widths):
+    # several n-tiles per problem (154 virtuals: 11781 pairs) and a ragged m edge
+    d = lno_ot.to_device(make_domain(160, (6, 4), naux=120, L=30.0, seed=2))
+    res = []
+    for bn in widths:
+        p = tmp_path / f"t{bn}.txt"
+        p.write_text(f"100000 {bn} 16\n")
+        ctx = lno_ot.Context(0, prec, tune_cache=str(p))
+        res.append(ctx.energy(d))
+        ctx.close()
+    for c in CASES + ("total",):
+        assert res[0][c] == res[1][c], (prec, c)
+
+
+@pytest.fixture(scope="module")
+def ctx15(lib):
+    c = lno_ot.Context(0, "bf16x15")
+    yield c
+    c.close()
+
+
+# BF16X15 removes the slicing error almost entirely; what is left per triplet
+# is the float32 rounding of the W intermediates and of the energy arithmetic
+# (about 1e-8 of e_t at c0), the same floor as BF16X10's
+def test_c0_bf16x15_per_triplet(ctx15):
+    g = golden("c0")
+    out, et = run_with_trip(ctx15, config_domain("c0"))
+    for i, c in enumerate(CASES):
+        assert np.abs(et[i] - np.array(g["cases"][c]["e"])).max() <= 1e-9, c
+    assert abs(out["total"] - g["total"]) <= 1e-8
+
+
+def test_c4_bf16x15_per_triplet(ctx15):
+    g = golden("c4")
+    out, et = run_with_trip(ctx15, config_domain("c4"))
+    worst = 0.0
+    for i, c in enumerate(CASES):
+        err = np.abs(et[i] - np.array(g["cases"][c]["e"])).max()
+        worst = max(worst, err)
+        assert err <= 2e-9, c
+    assert abs(out["total"] - g["total"]) <= 1e-8
+    print("c4 bf16x15 worst per-triplet |dE| =", worst)

@@ -39,7 +39,7 @@ def _call(fn, S, A, B):
 
 def test_noalloc_matches_allocating_entry_point_on_two_calls(lib):
     L = _bind(lib)
-    cases = [(3, 300, 700, 600, 1), (2, 200, 300, 40, 2)]
+    cases = [(4, 260, 500, 300, 3), (3, 300, 700, 600, 1), (2, 200, 300, 40, 2)]
     for S, M, N, K, seed in cases:
         rng = np.random.default_rng(seed)
         A = rng.standard_normal((M, K))
@@ -51,6 +51,24 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls(lib):
         assert np.isfinite(got).all()
         assert np.abs(got - ref).max() / scale < tol
         assert np.abs(got - B @ A.T).max() / scale < tol
+
+
+def test_noalloc_rejects_host_pointers_and_restores_device(lib):
+    L = _bind(lib)
+    dA = torch.zeros((64, 32), dtype=torch.float64, device="cuda")
+    dC = torch.zeros((64, 64), dtype=torch.float64, device="cuda")
+    host = np.zeros((64, 32))
+    dev0 = torch.cuda.current_device()
+    rc = L.lno_ot_gemm_sliced_noalloc(0, 2, 64, 64, 32, ctypes.c_void_p(dA.data_ptr()),
+                                      ctypes.c_void_p(host.ctypes.data),
+                                      ctypes.c_void_p(dC.data_ptr()), None)
+    assert rc == -2   # LNO_OT_EDEVICE: nothing was launched
+    assert torch.cuda.current_device() == dev0
+    # a bad device ordinal is rejected too
+    rc = L.lno_ot_gemm_sliced_noalloc(1 << 20, 2, 64, 64, 32, ctypes.c_void_p(dA.data_ptr()),
+                                      ctypes.c_void_p(dA.data_ptr()),
+                                      ctypes.c_void_p(dC.data_ptr()), None)
+    assert rc == -2
 
 
 def test_noalloc_rejects_oversized_operands(lib):
