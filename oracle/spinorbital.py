@@ -184,3 +184,45 @@ def orbital_partition(dom):
             one_t = e[o_s][:, o_t][:, :, v_s][:, :, :, v_s][:, :, :, :, v_t].sum() / 8.0
             res["alpha" if s == 0 else "beta"].append(float(same + two_t + one_t))
         return res
+
+
+def central_energy_brute(dom, spin, U, s, w):
+    """eq local_pt written out over spin orbitals (tiny inputs only).
+
+    For a central orbital u = sum_i U[l, i] phi_i (i over the occupied
+    orbitals of ``spin``) and the quadrature (s_q, w_q) of eq laplace_transform:
+
+      dE_u = -sum_q w_q (1/36) sum_{jkabc} Wbar_u (Wbar_u + Vbar_u),
+      Wbar_u[jkabc] = sum_i U[l,i] e^{e_i s_q/2} W[ijkabc] e^{(e_j+e_k) s_q/2}
+                      e^{-(e_a+e_b+e_c) s_q/2}
+
+    over unrestricted spin-orbital j, k, a, b, c (the first-index share of the
+    1/36 sum of the definition, whose denominators the quadrature replaces).
+    Returns a list [nlmo].
+    """
+    d = dom if isinstance(dom["B"][0], torch.Tensor) else as_tensors(dom)
+    _, t = brute_force(d, return_tensors=True)
+    W, V, occ, vir = t["W"], t["V"], t["occ"], t["vir"]
+    U = torch.as_tensor(U, dtype=_f64)
+    eo = torch.stack([d["eps"][x][p] for x, p in occ])
+    ev = torch.stack([d["eps"][x][p] for x, p in vir])
+    rows = [I for I, (x, _) in enumerate(occ) if x == spin]   # occupied spin orbitals of `spin`
+    out = [0.0] * U.shape[0]
+    with torch.no_grad():
+        for sq, wq in zip(s, w):
+            sq, wq = float(sq), float(wq)
+            f = (torch.exp(eo * sq / 2)[:, None, None, None, None]
+                 * torch.exp(eo * sq / 2)[None, :, None, None, None]
+                 * torch.exp(-ev * sq / 2)[None, None, :, None, None]
+                 * torch.exp(-ev * sq / 2)[None, None, None, :, None]
+                 * torch.exp(-ev * sq / 2)[None, None, None, None, :])
+            for l in range(U.shape[0]):
+                Wb = torch.zeros_like(W[0])
+                Vb = torch.zeros_like(V[0])
+                for q, I in enumerate(rows):
+                    c = U[l, q] * torch.exp(eo[I] * sq / 2)
+                    Wb = Wb + c * W[I]
+                    Vb = Vb + c * V[I]
+                Wb, Vb = Wb * f, Vb * f
+                out[l] += -wq * float((Wb * (Wb + Vb)).sum()) / 36.0
+    return out
