@@ -223,6 +223,50 @@ LNO_OT_API int lno_ot_energy_batched(lno_ot_ctx* ctx, int ndom, const lno_ot_dom
 LNO_OT_API int lno_ot_backward(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE,
                     lno_ot_grad* g);
 
+/* Central-LMO share of E(T) in the Laplace form (Sec. 3.7, eqs
+ * laplace_transform and local_pt).  The denominators are replaced by the
+ * quadrature 1/Delta ~ sum_q w_q exp(-Delta s_q) (Delta = -D > 0), after
+ * which the sum over the first occupied index is a trace and can be taken in
+ * a basis of localized orbitals.  For each central orbital u (row l of U: its
+ * coefficients in the semicanonical occupied orbitals of spin `spin`) the
+ * call returns
+ *
+ *   dE[l] = -(1/3) sum_q w_q [ sum_{j<k, a<b<c} Wbar (Wbar + Vbar)_{u j k}
+ *                             + sum_{j, K, a<b, C} ... + sum_{J<K, A<B, c} ... ]
+ *
+ * the i' (spin 0) or I' (spin 1) terms of eq local_pt: every triplet that
+ * holds u, with 1/3 of it to u, and the bars exp(+e_p s_q/2) per occupied and
+ * exp(-e_x s_q/2) per virtual index.  The share of a spatial LMO is
+ * dE of its spin-up part plus dE of its spin-down part.  Over a complete
+ * orthonormal set of central orbitals of both spins the shares add up to the
+ * Laplace-quadrature E(T) of the domain, which tends to E(T) as the
+ * quadrature gets accurate.  Cost O(nq no^2 nv^4) per central orbital.  The
+ * domain's trip_sel, e_trip and e_orb members are ignored.  Runs in the
+ * context's precision; results in host memory on return. */
+typedef struct {
+  int nq;                 /* quadrature points, 1..32 */
+  const double* s;        /* HOST [nq] points s_q > 0 (1/Eh) */
+  const double* w;        /* HOST [nq] weights w_q */
+  int spin;               /* 0: central orbitals of spin up, 1: spin down */
+  int nlmo;               /* number of central orbitals (>= 0) */
+  const double* U;        /* DEVICE [nlmo][nocc[spin]] coefficients (rows) */
+  double* dE;             /* HOST out [nlmo] (Eh) */
+} lno_ot_central;
+
+LNO_OT_API int lno_ot_energy_central(lno_ot_ctx* ctx, const lno_ot_domain* dom,
+                                     const lno_ot_central* c);
+
+/* Quadrature for the Laplace form (host only, no device work): the fewest
+ * points n <= nmax (<= 32) whose sum_q w_q exp(-x s_q) approximates 1/x with a
+ * largest relative error <= tol on [xmin, xmax] (0 < xmin < xmax; the range of
+ * Delta over the domain's triples).  The paper fixes the tolerance (laptol =
+ * 1e-2, Table thresholds, giving 3-4 points) but not the construction: here a
+ * least-squares fit of the relative error, reweighted towards the minimax
+ * fit, from a trapezoid start.  s, w: HOST [nmax]; *nq = n.  Returns
+ * LNO_OT_EUNSUPPORTED if nmax points do not reach tol. */
+LNO_OT_API int lno_ot_laplace_quadrature(double xmin, double xmax, double tol, int nmax,
+                                         double* s, double* w, int* nq);
+
 /* Stats of the last lno_ot_energy on this context. */
 LNO_OT_API int lno_ot_last_stats(const lno_ot_ctx* ctx, lno_ot_stats* st);
 

@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUTDIR, "liblno_ot.so")
-SOURCES = ["lno_ot.cu", "gemm_f64.cu", "energy.cu", "pack.cu", "tc_gemm.cu", "noalloc.cu", "backward.cu"]
+SOURCES = ["lno_ot.cu", "gemm_f64.cu", "energy.cu", "pack.cu", "tc_gemm.cu", "noalloc.cu",
+           "backward.cu", "central.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -74,6 +74,10 @@ struct EnergyArgs {
   int64_t z_stride;    // between consecutive ZT
   const Trip* trips;   // [ntrip]
   double* partial;     // [ntrip][gridDim.x]
+  // Laplace form (Sec. 3.7, eq laplace_transform): with lap_w != 0 the
+  // kernels weight each element by -lap_w exp(lap_s D) instead of 1/D (one
+  // quadrature point of 1/D = -sum_q w_q exp(s_q D), D < 0)
+  double lap_s, lap_w;
 };
 
 // (px|ry) of spin s in the slot-compacted [ns][nvs][ns][nvs] block
@@ -92,6 +96,9 @@ struct OrbPartArgs {
   int64_t n[4];
   int na, nb;
   double* out[2];       // [na], [nb] (either may be NULL)
+  // 0: the prefactors of eq cim_pt_energy (mixed triplet 1/4, 1/4, 1/2);
+  // 1: eq local_pt's 1/3 of every triplet to each of its orbitals
+  int thirds;
 };
 
 // V plane on two spin-s virtuals: vmode 0 <pr||xy> = (px|ry) - (py|rx),
@@ -144,6 +151,25 @@ int sliced_product_bn(int S);
 cudaError_t launch_sliced_product(int S, const CUtensorMap* mA, const CUtensorMap* mB,
                                   const TcProb* dp, int M, int N, double scale, int* flag,
                                   int nsm, cudaStream_t st, TcDiag dg);
+
+// Augmented domain of the central-LMO pass (central.cu): P pseudo-orbitals
+// appended after the occupied orbitals of spin `spin`, for quadrature point s.
+struct AugmentArgs {
+  int spin, P, nbas, naux, nocc[2];
+  double s;
+  const double* U;        // [P][nocc[spin]] LMO coefficients
+  const double* B_in;     // [naux][nbas][nbas] of `spin`
+  const double* eps_in;   // [nbas]
+  const double* t1_in;    // [nocc][nvir]
+  const double* fov_in;   // [nocc][nvir] or NULL
+  const double* t2ss_in;  // same-spin doubles of `spin`
+  const double* t2ab_in;  // [na][nb][va][vb]
+  double* coef;           // [P][nocc[spin]]
+  double *B_out, *eps_out, *t1_out, *fov_out, *t2ss_out, *t2ab_out;
+};
+cudaError_t launch_lmo_augment(const AugmentArgs& A, cudaStream_t st);
+int laplace_quadrature(double xmin, double xmax, double tol, int nmax, double* s, double* w,
+                       int* nq);
 
 // Operand stores used by the layout kernels.  `part` says whether the value
 // is an amplitude (0) or an integral (1): the two have separate scales.

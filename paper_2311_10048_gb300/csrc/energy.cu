@@ -232,7 +232,8 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
                   t1s[6][cl] * vt[4][al][bl];
             }
             const double D = dbc - ev[0][al];
-            acc += (FM ? w * v : w * (w + v)) / D;
+            const double num = FM ? w * v : w * (w + v);
+            acc += a.lap_w != 0.0 ? num * (-a.lap_w * exp(a.lap_s * D)) : num / D;
           }
         } else {
           const TwoF dd = split_df(dbc);
@@ -258,7 +259,9 @@ energy_group(EnergyArgs a, const T* __restrict__ X, const T* __restrict__ Z) {
             }
             const float num = FM ? __fmul_rn(w, v) : __fmul_rn(w, __fadd_rn(w, v));
             const float D = df_sub_round(dd, split_df(ev[0][al]));
-            part = __fadd_rn(part, __fdiv_rn(num, D));
+            part = __fadd_rn(part, a.lap_w != 0.0
+                                       ? num * (float)(-a.lap_w * exp(a.lap_s * (double)D))
+                                       : __fdiv_rn(num, D));
           }
           acc += (double)part;
         }
@@ -350,6 +353,11 @@ __device__ __forceinline__ float div_nr(float num, float D) {
   return __fmul_rn(num, r);
 }
 
+// Laplace weight -w exp(s D) of one element (D < 0, so the argument is <= 0).
+__device__ __forceinline__ float lap_weight(float nw, float s, float D) {
+  return __fmul_rn(nw, expf(__fmul_rn(s, D)));
+}
+
 // Energy of float32 X with register prefetch of the next cube tile.
 // Work split inside a 16^3 tile: thread (c, b-pair, a-half) computes the 16
 // elements a in [8h, 8h+8), b in {2p, 2p+1}, c; values that depend on a only
@@ -361,7 +369,7 @@ __device__ __forceinline__ float div_nr(float num, float D) {
 // FU (mixed spin only): V = V(T1) + V(f_ov) in one pass; the f_ov planes sit
 // vt_half floats after the T1 planes of each triplet's table and the f_ov
 // coefficients come from a.fs / a.ft.
-template <bool MIXED, bool FM, bool FU>
+template <bool MIXED, bool FM, bool FU, bool LAP>
 __global__ void __launch_bounds__(256, 2)
 energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ Z,
            const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt, int64_t vt_half) {
@@ -402,6 +410,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   const int nvs = a.nvs, nvt = a.nvt;
   const TwoF eocc = split_df(MIXED ? a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_t[tr.k]
                                    : a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_s[tr.k]);
+  const float lnw = (float)(-a.lap_w), ls = (float)a.lap_s;   // Laplace weight (LAP only)
 
   float4 xr[3][4];
   float vr[9];
@@ -634,7 +643,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
               float s, e;
               two_sum(dbc[sb].hi, -da.w, s, e);
               const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc[sb].lo, del)));
-              const float qv = div_nr(num, D);
+              const float qv = LAP ? __fmul_rn(num, lap_weight(lnw, ls, D)) : div_nr(num, D);
               part = __fadd_rn(part, valid ? qv : 0.f);
             }
           }
@@ -674,7 +683,8 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
                   float s, e;
                   two_sum(dbc[sb].hi, -da.w, s, e);
                   const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc[sb].lo, del)));
-                  part = __fadd_rn(part, div_nr(num, D));
+                  part = __fadd_rn(part, LAP ? __fmul_rn(num, lap_weight(lnw, ls, D))
+                                             : div_nr(num, D));
                 }
               }
             }
@@ -723,7 +733,8 @@ __global__ void reduce_partials(const double* __restrict__ partial, int np,
 
 // Orbital contributions of eq cim_pt_energy from per-triplet contributions:
 // same-spin triplet 1/3 to each of its orbitals; mixed triplet 1/4 to each of
-// its two same-spin orbitals and 1/2 to the third.  One CTA per occupied
+// its two same-spin orbitals and 1/2 to the third (A.thirds: 1/3 each, the
+// partition of eq local_pt).  One CTA per occupied
 // orbital (spin up first), fixed-order Neumaier sums: bitwise reproducible.
 __global__ void orbital_partition(OrbPartArgs A) {
   __shared__ double ss[256], cc[256];
@@ -747,9 +758,9 @@ __global__ void orbital_partition(OrbPartArgs A) {
       if (same) {
         if (s == pair_spin && (t.i == p || t.j == p || t.k == p)) add(e[q] / 3.0);
       } else if (s == pair_spin) {
-        if (t.i == p || t.j == p) add(e[q] * 0.25);
+        if (t.i == p || t.j == p) add(A.thirds ? e[q] / 3.0 : e[q] * 0.25);
       } else if (t.k == p) {
-        add(e[q] * 0.5);
+        add(A.thirds ? e[q] / 3.0 : e[q] * 0.5);
       }
     }
   }
@@ -808,17 +819,23 @@ cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* 
   dim3 gp(64, ntrip);
   energy_prep<<<gp, 256, 0, st>>>(a, vtab, vt_stride, pv, pvt);
   dim3 grid(nchunks, ntrip);
+#define LNO_EF32(M, F, L) \
+  energy_f32<M, F, false, L><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0)
+  const bool lap = a.lap_w != 0.0;
   if (a.kind == SAME) {
-    if (a.vmode)
-      energy_f32<false, true, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0);
-    else
-      energy_f32<false, false, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0);
+    if (a.vmode) {
+      if (lap) LNO_EF32(false, true, true); else LNO_EF32(false, true, false);
+    } else {
+      if (lap) LNO_EF32(false, false, true); else LNO_EF32(false, false, false);
+    }
   } else {
-    if (a.vmode)
-      energy_f32<true, true, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0);
-    else
-      energy_f32<true, false, false><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0);
+    if (a.vmode) {
+      if (lap) LNO_EF32(true, true, true); else LNO_EF32(true, true, false);
+    } else {
+      if (lap) LNO_EF32(true, false, true); else LNO_EF32(true, false, false);
+    }
   }
+#undef LNO_EF32
   return cudaGetLastError();
 }
 
@@ -847,8 +864,12 @@ cudaError_t launch_energy_f32_fused(const EnergyArgs& a, const float* X, const f
   energy_prep<<<gp, 256, 0, st>>>(a0, vtab, 2 * vt_half, pv, pvt);
   energy_prep<<<gp, 256, 0, st>>>(a1, vtab + vt_half, 2 * vt_half, pv, pvt);
   dim3 grid(nchunks, ntrip);
-  energy_f32<true, false, true><<<grid, 256, 0, st>>>(a0, X, Z, vtab, 2 * vt_half, pv, pvt,
-                                                      vt_half);
+  if (a.lap_w != 0.0)
+    energy_f32<true, false, true, true><<<grid, 256, 0, st>>>(a0, X, Z, vtab, 2 * vt_half, pv,
+                                                             pvt, vt_half);
+  else
+    energy_f32<true, false, true, false><<<grid, 256, 0, st>>>(a0, X, Z, vtab, 2 * vt_half, pv,
+                                                              pvt, vt_half);
   return cudaGetLastError();
 }
 

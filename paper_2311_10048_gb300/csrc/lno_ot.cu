@@ -47,22 +47,22 @@ template <class St>
 cudaError_t launch_transpose_block(const double*, int, int, int, int, int, int, int, St,
                                    cudaStream_t);
 template <class St>
-cudaError_t launch_pack_at_same(const int2*, int, int, int, int, const double*, const double*, St,
+cudaError_t launch_pack_at_same(const int2*, int, int, int, int, int, const double*, const double*,
+                                St, cudaStream_t);
+template <class St>
+cudaError_t launch_pack_bt_same(int, int, int, int, int, int, const double*, const double*, St,
                                 cudaStream_t);
 template <class St>
-cudaError_t launch_pack_bt_same(int, int, int, int, int, const double*, const double*, St,
-                                cudaStream_t);
-template <class St>
-cudaError_t launch_pack_a1(const int2*, int, int, int, int, int, int, const double*,
+cudaError_t launch_pack_a1(const int2*, int, int, int, int, int, int, int, const double*,
                            const double*, St, cudaStream_t);
 template <class St>
-cudaError_t launch_pack_bg(int, int, int, int, int, int, int, const double*, const double*, St,
-                           cudaStream_t);
+cudaError_t launch_pack_bg(int, int, int, int, int, int, int, int, const double*, const double*,
+                           St, cudaStream_t);
 template <class St>
-cudaError_t launch_pack_bf(int, int, int, int, int, int, int, const double*, const double*, St,
-                           cudaStream_t);
+cudaError_t launch_pack_bf(int, int, int, int, int, int, int, int, const double*, const double*,
+                           St, cudaStream_t);
 template <class St>
-cudaError_t launch_pack_at2(const int2*, int, int, int, int, int, int, const double*,
+cudaError_t launch_pack_at2(const int2*, int, int, int, int, int, int, int, const double*,
                             const double*, St, cudaStream_t);
 cudaError_t launch_transpose_t2ab(const double*, int, int, int, int, double*, cudaStream_t);
 cudaError_t launch_absmax(const double*, int64_t, unsigned long long*, cudaStream_t);
@@ -273,7 +273,15 @@ struct Run {
   bool amax_pass = false;  // true while measuring integral magnitudes
   double amax_int = 0.0;
   int nbas, naux, no[2], nv[2];
-  // DF factor blocks per spin (rows, K = naux)
+  // orbitals per spin: nbas, or nbas + P for a spin that carries P central
+  // pseudo-orbitals (set before stage(); 0 = nbas)
+  int nbs[2] = {0, 0};
+  // occupied orbitals the internal (summed) indices run over: no[s] unless
+  // pseudo-orbitals (central LMOs, Sec. 3.7) follow the real ones
+  int noi[2] = {-1, -1};
+  // Laplace quadrature point of the central-LMO pass (lap_w = 0: 1/D)
+  double lap_s = 0.0, lap_w = 0.0;
+  // DF factor blocks per spin (rows, K = naux); Boo rows are [internal][external]
   Operand Boo[2], Bov[2], Bvv[2];
   const double* fov[2] = {nullptr, nullptr};  // f_ov blocks (both or none)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> contract_ev, energy_ev;
@@ -364,13 +372,15 @@ struct Run {
     nbas = dom->nbas;
     naux = dom->naux;
     for (int s = 0; s < 2; ++s) {
+      if (nbs[s] <= 0) nbs[s] = nbas;
       no[s] = dom->nocc[s];
-      nv[s] = nbas - no[s];
+      nv[s] = nbs[s] - no[s];
+      if (noi[s] < 0 || noi[s] > no[s]) noi[s] = no[s];
     }
     if (!f64) {  // global scales of B and T2
       CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), st));
       for (int s = 0; s < 2; ++s)
-        CU(launch_absmax(dom->B[s], (int64_t)naux * nbas * nbas, ctx->d_amax, st));
+        CU(launch_absmax(dom->B[s], (int64_t)naux * nbs[s] * nbs[s], ctx->d_amax, st));
       unsigned long long h;
       CU(cudaMemcpyAsync(&h, ctx->d_amax, sizeof h, cudaMemcpyDeviceToHost, st));
       CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), st));
@@ -401,26 +411,26 @@ struct Run {
       }
     }
     for (int s = 0; s < 2; ++s) {
-      const int o = no[s], v = nv[s];
-      TRY(alloc_operand(Boo[s], 1, (int64_t)o * o, naux, Sdf));
+      const int o = no[s], oi = noi[s], v = nv[s];
+      TRY(alloc_operand(Boo[s], 1, (int64_t)oi * o, naux, Sdf));
       TRY(alloc_operand(Bov[s], 1, (int64_t)o * v, naux, Sdf));
       TRY(alloc_operand(Bvv[s], 1, (int64_t)v * v, naux, Sdf));
       struct Blk {
         Operand* op;
         int p0, np, q0, nq;
-      } blks[3] = {{&Boo[s], 0, o, 0, o}, {&Bov[s], 0, o, o, v}, {&Bvv[s], o, v, o, v}};
+      } blks[3] = {{&Boo[s], 0, oi, 0, o}, {&Bov[s], 0, o, o, v}, {&Bvv[s], o, v, o, v}};
       for (auto& b : blks) {
         stats->other_launches++;
         if (f64)
-          CU(launch_transpose_block(dom->B[s], naux, nbas, b.p0, b.np, b.q0, b.nq, b.op->Kp,
+          CU(launch_transpose_block(dom->B[s], naux, nbs[s], b.p0, b.np, b.q0, b.nq, b.op->Kp,
                                     StoreF64{b.op->f64}, st));
         else if (Sdf == 5)
           CU(launch_transpose_block(
-              dom->B[s], naux, nbas, b.p0, b.np, b.q0, b.nq, b.op->Kp,
+              dom->B[s], naux, nbs[s], b.p0, b.np, b.q0, b.nq, b.op->Kp,
               StoreSlices<5>{b.op->bf, b.op->slice_stride, 128.0 / sigB, 128.0 / sigB}, st));
         else
           CU(launch_transpose_block(
-              dom->B[s], naux, nbas, b.p0, b.np, b.q0, b.nq, b.op->Kp,
+              dom->B[s], naux, nbs[s], b.p0, b.np, b.q0, b.nq, b.op->Kp,
               StoreSlices<4>{b.op->bf, b.op->slice_stride, 128.0 / sigB, 128.0 / sigB}, st));
       }
     }
@@ -522,6 +532,7 @@ struct SpinPass {
   Run& R;
   int s, t;
   int o, v, ot, vt;
+  int oi, oti;  // internal occupied ranges (== o, ot without pseudo-orbitals)
   CaseSel& same;   // case s==0 ? aaa : bbb
   CaseSel& mixed;  // case s==0 ? aab : abb
   double* e_same;  // per-triplet outputs (device)
@@ -555,6 +566,8 @@ struct SpinPass {
     v = R.nv[s];
     ot = R.no[t];
     vt = R.nv[t];
+    oi = R.noi[s];
+    oti = R.noi[t];
   }
 
   void plan() {
@@ -612,15 +625,15 @@ struct SpinPass {
     // ---- same-spin operands -------------------------------------------------
     if (!listAT.empty()) {
       double* oovoT;
-      TRY(A.get(&oovoT, (size_t)o * v * o * o));
-      TRY(R.df(R.Boo[s], 0, o * o, R.Bov[s], 0, o * v, oovoT, o * o));
+      TRY(A.get(&oovoT, (size_t)o * v * oi * o));
+      TRY(R.df(R.Boo[s], 0, oi * o, R.Bov[s], 0, o * v, oovoT, oi * o));
       if (!R.amax_pass) {
         int2* dl;
         TRY(A.get(&dl, listAT.size()));
         CU(cudaMemcpyAsync(dl, listAT.data(), listAT.size() * sizeof(int2),
                            cudaMemcpyHostToDevice, st));
         R.stats->other_launches++;
-        CU(launch_pack_at_same(dl, (int)listAT.size(), o, v, AT.Kp, t2ss, oovoT, stAT, st));
+        CU(launch_pack_at_same(dl, (int)listAT.size(), o, oi, v, AT.Kp, t2ss, oovoT, stAT, st));
       }
       A.drop(oovoT);
     }
@@ -632,7 +645,7 @@ struct SpinPass {
         TRY(R.df(R.Bvv[s], 0, v * v, R.Bov[s], (int64_t)x * v, v, vvovT, v * v));
         if (!R.amax_pass) {
           R.stats->other_launches++;
-          CU(launch_pack_bt_same((int)q, x, o, v, BT.Kp, vvovT, t2ss, stBT, st));
+          CU(launch_pack_bt_same((int)q, x, o, oi, v, BT.Kp, vvovT, t2ss, stBT, st));
         }
       }
       A.drop(vvovT);
@@ -640,15 +653,15 @@ struct SpinPass {
     // ---- mixed operands -----------------------------------------------------
     if (!listA1.empty()) {
       double* jT;
-      TRY(A.get(&jT, (size_t)o * v * ot * ot));
-      TRY(R.df(R.Bov[s], 0, o * v, R.Boo[t], 0, ot * ot, jT, o * v));
+      TRY(A.get(&jT, (size_t)o * v * oti * ot));
+      TRY(R.df(R.Bov[s], 0, o * v, R.Boo[t], 0, oti * ot, jT, o * v));
       if (!R.amax_pass) {
         int2* dl;
         TRY(A.get(&dl, listA1.size()));
         CU(cudaMemcpyAsync(dl, listA1.data(), listA1.size() * sizeof(int2),
                            cudaMemcpyHostToDevice, st));
         R.stats->other_launches++;
-        CU(launch_pack_a1(dl, (int)listA1.size(), o, v, ot, vt, A1.Kp, t2st, jT, stA1, st));
+        CU(launch_pack_a1(dl, (int)listA1.size(), o, v, ot, oti, vt, A1.Kp, t2st, jT, stA1, st));
       }
       A.drop(jT);
     }
@@ -660,7 +673,7 @@ struct SpinPass {
         TRY(R.df(R.Bvv[t], 0, vt * vt, R.Bov[s], (int64_t)x * v, v, gT, vt * vt));
         if (!R.amax_pass) {
           R.stats->other_launches++;
-          CU(launch_pack_bg((int)q, x, o, v, ot, vt, BG.Kp, gT, t2st, stBG, st));
+          CU(launch_pack_bg((int)q, x, o, v, ot, oti, vt, BG.Kp, gT, t2st, stBG, st));
         }
       }
       A.drop(gT);
@@ -673,22 +686,23 @@ struct SpinPass {
         TRY(R.df(R.Bvv[s], 0, v * v, R.Bov[t], (int64_t)K * vt, vt, fT, v * v));
         if (!R.amax_pass) {
           R.stats->other_launches++;
-          CU(launch_pack_bf((int)q, K, o, v, ot, vt, BF.Kp, fT, t2st, stBF, st));
+          CU(launch_pack_bf((int)q, K, o, oi, v, ot, vt, BF.Kp, fT, t2st, stBF, st));
         }
       }
       A.drop(fT);
     }
     if (!listAT2.empty()) {
       double* lT;
-      TRY(A.get(&lT, (size_t)ot * vt * o * o));
-      TRY(R.df(R.Boo[s], 0, o * o, R.Bov[t], 0, ot * vt, lT, o * o));
+      TRY(A.get(&lT, (size_t)ot * vt * oi * o));
+      TRY(R.df(R.Boo[s], 0, oi * o, R.Bov[t], 0, ot * vt, lT, oi * o));
       if (!R.amax_pass) {
         int2* dl;
         TRY(A.get(&dl, listAT2.size()));
         CU(cudaMemcpyAsync(dl, listAT2.data(), listAT2.size() * sizeof(int2),
                            cudaMemcpyHostToDevice, st));
         R.stats->other_launches++;
-        CU(launch_pack_at2(dl, (int)listAT2.size(), o, v, ot, vt, AT2.Kp, t2st, lT, stAT2, st));
+        CU(launch_pack_at2(dl, (int)listAT2.size(), o, oi, v, ot, vt, AT2.Kp, t2st, lT, stAT2,
+                           st));
       }
       A.drop(lT);
     }
@@ -757,12 +771,12 @@ struct SpinPass {
   }
 
   int build() {
-    TRY(R.alloc_operand(own, AT, (int)listAT.size(), v, v + o, R.S));
-    TRY(R.alloc_operand(own, BT, (int)listBT.size(), npairs(v), v + o, R.S));
-    TRY(R.alloc_operand(own, A1, (int)listA1.size(), v, vt + ot, R.S));
-    TRY(R.alloc_operand(own, BG, (int)listBG.size(), (int64_t)v * vt, vt + ot, R.S));
-    TRY(R.alloc_operand(own, BF, (int)listBF.size(), (int64_t)v * vt, v + o, R.S));
-    TRY(R.alloc_operand(own, AT2, (int)listAT2.size(), vt, v + o, R.S));
+    TRY(R.alloc_operand(own, AT, (int)listAT.size(), v, v + oi, R.S));
+    TRY(R.alloc_operand(own, BT, (int)listBT.size(), npairs(v), v + oi, R.S));
+    TRY(R.alloc_operand(own, A1, (int)listA1.size(), v, vt + oti, R.S));
+    TRY(R.alloc_operand(own, BG, (int)listBG.size(), (int64_t)v * vt, vt + oti, R.S));
+    TRY(R.alloc_operand(own, BF, (int)listBF.size(), (int64_t)v * vt, v + oi, R.S));
+    TRY(R.alloc_operand(own, AT2, (int)listAT2.size(), vt, v + oi, R.S));
     if (R.f64) return pack_all(StoreF64{AT.f64}, StoreF64{BT.f64}, StoreF64{A1.f64},
                                StoreF64{BG.f64}, StoreF64{BF.f64}, StoreF64{AT2.f64});
     if (R.S == 2)
@@ -904,16 +918,20 @@ struct SpinPass {
     ea.pitch_z = P2;
     ea.x_stride = N1 * P1;
     ea.z_stride = N2 * P2;
+    ea.lap_s = R.lap_s;
+    ea.lap_w = R.lap_w;
 
     // stats
-    const double dv = v, dvt = vt, dov = o, dot = ot;
-    const double alg = is_mixed ? flops_alg_mixed(dv, dvt, dov, dot) : flops_alg_same(dv, dov);
-    const double exe = is_mixed ? 2.0 * dv * (dv * dvt) * (2 * (dvt + dot) + dv + dov) +
-                                      2.0 * dvt * (double)npairs(v) * 2 * (dv + dov)
-                                : 2.0 * dv * (double)npairs(v) * 3 * (dv + dov);
-    const double tens = is_mixed ? 2.0 * dv * (dv * dvt) * (2 * kpad16(dvt + dot) + kpad16(dv + dov)) +
-                                       2.0 * dvt * (double)npairs(v) * 2 * kpad16(dv + dov)
-                                 : 2.0 * dv * (double)npairs(v) * 3 * kpad16(dv + dov);
+    const double dv = v, dvt = vt;
+    const double alg = is_mixed ? flops_alg_mixed(dv, dvt, (double)oi, (double)oti)
+                                : flops_alg_same(dv, (double)oi);
+    const double doi = oi, doti = oti;   // K of the hole parts: the internal ranges
+    const double exe = is_mixed ? 2.0 * dv * (dv * dvt) * (2 * (dvt + doti) + dv + doi) +
+                                      2.0 * dvt * (double)npairs(v) * 2 * (dv + doi)
+                                : 2.0 * dv * (double)npairs(v) * 3 * (dv + doi);
+    const double tens = is_mixed ? 2.0 * dv * (dv * dvt) * (2 * kpad16(dvt + doti) + kpad16(dv + doi)) +
+                                       2.0 * dvt * (double)npairs(v) * 2 * kpad16(dv + doi)
+                                 : 2.0 * dv * (double)npairs(v) * 3 * kpad16(dv + doi);
     R.stats->flops_algorithmic += alg * ntrip;
     R.stats->flops_executed += exe * ntrip;
     if (!f64) R.stats->tensor_flops += tens * ntrip * (R.S * (R.S + 1) / 2);
@@ -1101,13 +1119,32 @@ int validate(const lno_ot_ctx* ctx, const lno_ot_domain* d) {
   return LNO_OT_OK;
 }
 
-int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
-  TRY(validate(ctx, dom));
+// Settings of an internal energy pass over an augmented domain (the central
+// LMOs of the Laplace form): explicit triplet lists, per-spin orbital counts,
+// internal occupied ranges, one quadrature point and eq local_pt's partition.
+struct PassSpec {
+  const CaseSel* cs;   // [4]
+  int nbs[2];
+  int noi[2];
+  double lap_s, lap_w;
+};
+
+int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out,
+                const PassSpec* spec = nullptr) {
+  if (!spec) TRY(validate(ctx, dom));
   if (ctx->prec == LNO_OT_TF32) return LNO_OT_EUNSUPPORTED;
   CU(cudaSetDevice(ctx->device));
-  ctx->stats = lno_ot_stats{};
+  if (!spec) ctx->stats = lno_ot_stats{};
   ctx->ev_used = 0;
   Run R(ctx, dom);
+  if (spec) {
+    for (int s = 0; s < 2; ++s) {
+      R.nbs[s] = spec->nbs[s];
+      R.noi[s] = spec->noi[s];
+    }
+    R.lap_s = spec->lap_s;
+    R.lap_w = spec->lap_w;
+  }
   R.f64 = ctx->prec == LNO_OT_FP64;
   R.S = ctx->prec == LNO_OT_BF16X6    ? 3
         : ctx->prec == LNO_OT_BF16X10 ? 4
@@ -1119,7 +1156,12 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
   if (t0) cudaEventRecord(t0, R.st);
 
   CaseSel cs[4];
-  for (int c = 0; c < 4; ++c) TRY(select_case(dom, c, cs[c]));
+  for (int c = 0; c < 4; ++c) {
+    if (spec)
+      cs[c] = spec->cs[c];
+    else
+      TRY(select_case(dom, c, cs[c]));
+  }
   double* e_int[4];
   for (int c = 0; c < 4; ++c)
     TRY(R.arena.get(&e_int[c], std::max<size_t>(cs[c].trips.size(), 1)));
@@ -1130,6 +1172,7 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
               dom->eps[0] == dom->eps[1] && dom->t1[0] == dom->t1[1] &&
               dom->t2aa == dom->t2bb && dom->fov[0] == dom->fov[1];
   for (int c = 0; c < 4; ++c) flip = flip && dom->trip_sel[c] == nullptr;
+  flip = flip && spec == nullptr;
   if (flip && dom->nocc[0] > 0 && dom->nocc[0] < dom->nbas) {
     // symmetric to within 1e-12 of the largest amplitude: amplitudes from a
     // closed-shell calculation agree with their spin-flip images to rounding
@@ -1201,6 +1244,7 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
     OrbPartArgs oa{};
     oa.na = dom->nocc[0];
     oa.nb = dom->nocc[1];
+    oa.thirds = spec != nullptr;
     oa.out[0] = dom->e_orb[0];
     oa.out[1] = dom->e_orb[1];
     for (int c = 0; c < 4; ++c) {
@@ -1247,6 +1291,128 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
   return LNO_OT_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Central-LMO share in the Laplace form (Sec. 3.7, eqs laplace_transform and
+// local_pt): per quadrature point, an augmented domain with one pseudo-orbital
+// per central orbital (central.cu), the triplets that hold exactly one of
+// them, the element weight -w_q exp(s_q D), and eq local_pt's 1/3 of each
+// triplet to the pseudo-orbital; the quadrature points are summed on the host.
+int central_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, const lno_ot_central* c) {
+  if (!c) return LNO_OT_EINVAL;
+  TRY(validate(ctx, dom));
+  if (c->nq < 1 || c->nq > 32 || !c->s || !c->w || c->spin < 0 || c->spin > 1 || c->nlmo < 0)
+    return LNO_OT_EINVAL;
+  if (c->nlmo > 0 && !c->dE) return LNO_OT_EINVAL;
+  for (int q = 0; q < c->nq; ++q)
+    if (!(c->s[q] > 0.0) || !std::isfinite(c->s[q]) || !std::isfinite(c->w[q]))
+      return LNO_OT_EINVAL;
+  if (ctx->prec == LNO_OT_TF32) return LNO_OT_EUNSUPPORTED;
+  const int sg = c->spin, tg = 1 - sg, P = c->nlmo;
+  const int nbas = dom->nbas, naux = dom->naux;
+  const int na = dom->nocc[0], nb = dom->nocc[1], o = dom->nocc[sg];
+  const int v = nbas - o;
+  for (int l = 0; l < P; ++l) c->dE[l] = 0.0;
+  if (P == 0) return LNO_OT_OK;
+  if (o == 0) return LNO_OT_EINVAL;
+  TRY(check_ptr(ctx, c->U, true));
+  CU(cudaSetDevice(ctx->device));
+  ctx->stats = lno_ot_stats{};
+  cudaStream_t st = ctx->stream;
+  Arena A(st, ctx->ws_limit);
+  // augmented arrays of spin sg
+  const int nb2 = nbas + P, o2 = o + P;
+  AugmentArgs ag{};
+  ag.spin = sg;
+  ag.P = P;
+  ag.nbas = nbas;
+  ag.naux = naux;
+  ag.nocc[0] = na;
+  ag.nocc[1] = nb;
+  ag.U = c->U;
+  ag.B_in = dom->B[sg];
+  ag.eps_in = dom->eps[sg];
+  ag.t1_in = dom->t1[sg];
+  ag.fov_in = dom->fov[sg];
+  ag.t2ss_in = sg == 0 ? dom->t2aa : dom->t2bb;
+  ag.t2ab_in = dom->t2ab;
+  const int va = nbas - na, vb = nbas - nb;
+  TRY(A.get(&ag.coef, (size_t)P * o));
+  TRY(A.get(&ag.B_out, (size_t)naux * nb2 * nb2));
+  TRY(A.get(&ag.eps_out, (size_t)nb2));
+  TRY(A.get(&ag.t1_out, (size_t)std::max(o2 * v, 1)));
+  if (ag.fov_in) TRY(A.get(&ag.fov_out, (size_t)std::max(o2 * v, 1)));
+  TRY(A.get(&ag.t2ss_out, (size_t)std::max<int64_t>((int64_t)o2 * o2 * v * v, 1)));
+  TRY(A.get(&ag.t2ab_out, (size_t)std::max<int64_t>(
+                              (int64_t)(sg == 0 ? o2 : na) * (sg == 0 ? nb : o2) * va * vb, 1)));
+  double* eorb;
+  TRY(A.get(&eorb, (size_t)o2));
+  // triplets holding exactly one pseudo-orbital (augmented indices o + p)
+  CaseSel cs[4];
+  const int ot = dom->nocc[tg];
+  for (int p = 0; p < P; ++p) {
+    const int u = o + p;
+    for (int j = 0; j < o; ++j)      // same spin: (j, k, u), j < k < u
+      for (int k = j + 1; k < o; ++k) cs[sg == 0 ? 0 : 3].trips.push_back(Trip{j, k, u});
+    for (int j = 0; j < o; ++j)      // u and j of spin sg, K of the other: (j, u; K)
+      for (int K = 0; K < ot; ++K) cs[sg == 0 ? 1 : 2].trips.push_back(Trip{j, u, K});
+    for (int J = 0; J < ot; ++J)     // J < K of the other spin, u the single: (J, K; u)
+      for (int K = J + 1; K < ot; ++K) cs[sg == 0 ? 2 : 1].trips.push_back(Trip{J, K, u});
+  }
+  lno_ot_domain ad = *dom;
+  ad.nocc[sg] = o2;
+  ad.B[sg] = ag.B_out;
+  ad.eps[sg] = ag.eps_out;
+  ad.t1[sg] = ag.t1_out;
+  if (ag.fov_in) ad.fov[sg] = ag.fov_out;
+  if (sg == 0)
+    ad.t2aa = ag.t2ss_out;
+  else
+    ad.t2bb = ag.t2ss_out;
+  ad.t2ab = ag.t2ab_out;
+  for (int k = 0; k < 4; ++k) {
+    ad.e_trip[k] = nullptr;
+    ad.trip_sel[k] = nullptr;
+    ad.n_sel[k] = 0;
+  }
+  ad.e_orb[sg] = eorb;
+  ad.e_orb[tg] = nullptr;
+  PassSpec spec{};
+  spec.cs = cs;
+  spec.nbs[sg] = nb2;
+  spec.nbs[tg] = nbas;
+  spec.noi[0] = na;
+  spec.noi[1] = nb;
+  std::vector<double> acc(P, 0.0), comp(P, 0.0), part(P);
+  double ms[4] = {0, 0, 0, 0};
+  for (int q = 0; q < c->nq; ++q) {
+    ag.s = c->s[q];
+    CU(launch_lmo_augment(ag, st));
+    ctx->stats.other_launches += 7;
+    spec.lap_s = c->s[q];
+    spec.lap_w = c->w[q];
+    lno_ot_result r;
+    TRY(energy_impl(ctx, &ad, &r, &spec));
+    ms[0] += ctx->stats.ms_total;
+    ms[1] += ctx->stats.ms_stage;
+    ms[2] += ctx->stats.ms_contract;
+    ms[3] += ctx->stats.ms_energy;
+    CU(cudaMemcpyAsync(part.data(), eorb + o, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost,
+                       st));
+    CU(cudaStreamSynchronize(st));
+    for (int l = 0; l < P; ++l) {   // Neumaier over the quadrature points, in order
+      const double x = part[l], t = acc[l] + x;
+      comp[l] += std::fabs(acc[l]) >= std::fabs(x) ? (acc[l] - t) + x : (x - t) + acc[l];
+      acc[l] = t;
+    }
+  }
+  for (int l = 0; l < P; ++l) c->dE[l] = acc[l] + comp[l];
+  ctx->stats.ms_total = ms[0];
+  ctx->stats.ms_stage = ms[1];
+  ctx->stats.ms_contract = ms[2];
+  ctx->stats.ms_energy = ms[3];
+  return LNO_OT_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Adjoint (float64).  Gradient accumulators of one domain (raw, unprojected).
@@ -1785,6 +1951,16 @@ int lno_ot_backward(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot
   if (!ctx || !dom || !g) return LNO_OT_EINVAL;
   if (!std::isfinite(gE)) return LNO_OT_EINVAL;
   return backward_impl(ctx, dom, gE, g);
+}
+
+int lno_ot_energy_central(lno_ot_ctx* ctx, const lno_ot_domain* dom, const lno_ot_central* c) {
+  if (!ctx) return LNO_OT_EINVAL;
+  return central_impl(ctx, dom, c);
+}
+
+int lno_ot_laplace_quadrature(double xmin, double xmax, double tol, int nmax, double* s,
+                              double* w, int* nq) {
+  return laplace_quadrature(xmin, xmax, tol, nmax, s, w, nq);
 }
 
 int lno_ot_last_stats(const lno_ot_ctx* ctx, lno_ot_stats* st) {

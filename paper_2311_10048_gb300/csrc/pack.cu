@@ -17,6 +17,11 @@
 //   Y[a,(bC)]   = A1[j][K].BG[i] - A1[i][K].BG[j] + AT[i][j].BF[K]
 //   Z'[C,(a<b)] = -AT2[j][K].BT[i] + AT2[i][K].BT[j]
 // Rows are padded with zeros to a pitch Kp (multiple of 8).
+// Occupied indices come in two ranges: the summed (internal) m, M run over the
+// first oi (oti) orbitals, the external ones over all o (ot) the arrays hold.
+// The two differ only when pseudo-orbitals (the central LMOs of the Laplace
+// form, Sec. 3.7) are appended after the real occupied orbitals; the DF
+// blocks with one internal occupied index are laid out [internal][external].
 //
 // Every pack kernel is templated on its store: float64, or the exact
 // BF16 slices of the tensor-core path (value = scale 2^-7 (s1 + s2 + s3),
@@ -56,9 +61,9 @@ __global__ void transpose_block(const double* __restrict__ B, int naux, int nbas
 
 // AT[slot][a][kk] for same-spin pair (p,q) = pairs[slot]
 template <class St>
-__global__ void pack_at_same(const int2* __restrict__ pairs, int nslot, int o, int v, int Kp,
-                             const double* __restrict__ t2ss, const double* __restrict__ oovoT,
-                             St st) {
+__global__ void pack_at_same(const int2* __restrict__ pairs, int nslot, int o, int oi, int v,
+                             int Kp, const double* __restrict__ t2ss,
+                             const double* __restrict__ oovoT, St st) {
   const int64_t total = (int64_t)nslot * v * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -70,9 +75,9 @@ __global__ void pack_at_same(const int2* __restrict__ pairs, int nslot, int o, i
     double val = 0.0;
     if (kk < v) {
       val = t2ss[(((int64_t)pq.x * o + pq.y) * v + a) * v + kk];
-    } else if (kk < v + o) {
+    } else if (kk < v + oi) {
       const int m = kk - v;
-      const int64_t oo = (int64_t)o * o;
+      const int64_t oo = (int64_t)oi * o;
       // H_qp[m][a] = (mq|ap) - (mp|aq);  oovoT[(y*v+a)][(m*o+x)] = (mx|ya)
       val = oovoT[((int64_t)pq.x * v + a) * oo + m * o + pq.y] -
             oovoT[((int64_t)pq.y * v + a) * oo + m * o + pq.x];
@@ -83,7 +88,7 @@ __global__ void pack_at_same(const int2* __restrict__ pairs, int nslot, int o, i
 
 // BT[slot][pair(b<c)][kk] for occupied x; vvovT[c][(e*v+b)] = (eb|xc)
 template <class St>
-__global__ void pack_bt_same(int slot, int x, int o, int v, int Kp,
+__global__ void pack_bt_same(int slot, int x, int o, int oi, int v, int Kp,
                              const double* __restrict__ vvovT, const double* __restrict__ t2ss,
                              St st) {
   const int64_t np = npairs(v);
@@ -102,7 +107,7 @@ __global__ void pack_bt_same(int slot, int x, int o, int v, int Kp,
     double val = 0.0;
     if (kk < v) {
       val = vvovT[(int64_t)c * vv + (int64_t)kk * v + b] - vvovT[(int64_t)b * vv + (int64_t)kk * v + c];
-    } else if (kk < v + o) {
+    } else if (kk < v + oi) {
       const int m = kk - v;
       val = t2ss[(((int64_t)x * o + m) * v + b) * v + c];
     }
@@ -112,9 +117,9 @@ __global__ void pack_bt_same(int slot, int x, int o, int v, int Kp,
 
 // A1[slot][a][kk] for mixed pair (p,K) = pk[slot]; jT[(M*ot+K)][(p*vs+a)] = (pa|MK)
 template <class St>
-__global__ void pack_a1(const int2* __restrict__ pk, int nslot, int os, int vs, int ot, int vt,
-                        int Kp, const double* __restrict__ t2st, const double* __restrict__ jT,
-                        St st) {
+__global__ void pack_a1(const int2* __restrict__ pk, int nslot, int os, int vs, int ot, int oti,
+                        int vt, int Kp, const double* __restrict__ t2st,
+                        const double* __restrict__ jT, St st) {
   const int64_t total = (int64_t)nslot * vs * Kp;
   const int64_t ld = (int64_t)os * vs;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -126,7 +131,7 @@ __global__ void pack_a1(const int2* __restrict__ pk, int nslot, int os, int vs, 
     double val = 0.0;
     if (kk < vt) {
       val = -t2st[(((int64_t)p.x * ot + p.y) * vs + a) * vt + kk];
-    } else if (kk < vt + ot) {
+    } else if (kk < vt + oti) {
       const int M = kk - vt;
       val = jT[((int64_t)M * ot + p.y) * ld + (int64_t)p.x * vs + a];
     }
@@ -136,7 +141,7 @@ __global__ void pack_a1(const int2* __restrict__ pk, int nslot, int os, int vs, 
 
 // BG[slot][(b*vt+C)][kk] for occupied x (spin s); gT[b][(E*vt+C)] = (xb|EC)
 template <class St>
-__global__ void pack_bg(int slot, int x, int os, int vs, int ot, int vt, int Kp,
+__global__ void pack_bg(int slot, int x, int os, int vs, int ot, int oti, int vt, int Kp,
                         const double* __restrict__ gT, const double* __restrict__ t2st, St st) {
   const int64_t rows = (int64_t)vs * vt;
   const int64_t total = rows * Kp;
@@ -150,7 +155,7 @@ __global__ void pack_bg(int slot, int x, int os, int vs, int ot, int vt, int Kp,
     double val = 0.0;
     if (kk < vt) {
       val = gT[(int64_t)b * vv + (int64_t)kk * vt + C];
-    } else if (kk < vt + ot) {
+    } else if (kk < vt + oti) {
       const int M = kk - vt;
       val = t2st[(((int64_t)x * ot + M) * vs + b) * vt + C];
     }
@@ -160,7 +165,7 @@ __global__ void pack_bg(int slot, int x, int os, int vs, int ot, int vt, int Kp,
 
 // BF[slot][(b*vt+C)][kk] for occupied K (spin t); fT[C][(b*vs+e)] = (be|KC)
 template <class St>
-__global__ void pack_bf(int slot, int K, int os, int vs, int ot, int vt, int Kp,
+__global__ void pack_bf(int slot, int K, int os, int osi, int vs, int ot, int vt, int Kp,
                         const double* __restrict__ fT, const double* __restrict__ t2st, St st) {
   const int64_t rows = (int64_t)vs * vt;
   const int64_t total = rows * Kp;
@@ -174,7 +179,7 @@ __global__ void pack_bf(int slot, int K, int os, int vs, int ot, int vt, int Kp,
     double val = 0.0;
     if (kk < vs) {
       val = fT[(int64_t)C * vv + (int64_t)b * vs + kk];
-    } else if (kk < vs + os) {
+    } else if (kk < vs + osi) {
       const int m = kk - vs;
       val = -t2st[(((int64_t)m * ot + K) * vs + b) * vt + C];
     }
@@ -184,11 +189,11 @@ __global__ void pack_bf(int slot, int K, int os, int vs, int ot, int vt, int Kp,
 
 // AT2[slot][C][kk] for (p,K) = pk[slot]; lT[(K*vt+C)][(m*os+p)] = (mp|KC)
 template <class St>
-__global__ void pack_at2(const int2* __restrict__ pk, int nslot, int os, int vs, int ot, int vt,
-                         int Kp, const double* __restrict__ t2st, const double* __restrict__ lT,
-                         St st) {
+__global__ void pack_at2(const int2* __restrict__ pk, int nslot, int os, int osi, int vs, int ot,
+                         int vt, int Kp, const double* __restrict__ t2st,
+                         const double* __restrict__ lT, St st) {
   const int64_t total = (int64_t)nslot * vt * Kp;
-  const int64_t ld = (int64_t)os * os;
+  const int64_t ld = (int64_t)osi * os;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int kk = (int)(idx % Kp);
@@ -198,7 +203,7 @@ __global__ void pack_at2(const int2* __restrict__ pk, int nslot, int os, int vs,
     double val = 0.0;
     if (kk < vs) {
       val = t2st[(((int64_t)p.x * ot + p.y) * vs + kk) * vt + C];
-    } else if (kk < vs + os) {
+    } else if (kk < vs + osi) {
       const int m = kk - vs;
       val = lT[((int64_t)p.y * vt + C) * ld + (int64_t)m * os + p.x];
     }
@@ -301,56 +306,57 @@ cudaError_t launch_transpose_block(const double* B, int naux, int nbas, int p0, 
 }
 
 template <class St>
-cudaError_t launch_pack_at_same(const int2* pairs, int nslot, int o, int v, int Kp,
+cudaError_t launch_pack_at_same(const int2* pairs, int nslot, int o, int oi, int v, int Kp,
                                 const double* t2ss, const double* oovoT, St st, cudaStream_t s) {
   int64_t n = (int64_t)nslot * v * Kp;
   if (n == 0) return cudaSuccess;
-  pack_at_same<<<grid_for(n), 256, 0, s>>>(pairs, nslot, o, v, Kp, t2ss, oovoT, st);
+  pack_at_same<<<grid_for(n), 256, 0, s>>>(pairs, nslot, o, oi, v, Kp, t2ss, oovoT, st);
   return cudaGetLastError();
 }
 
 template <class St>
-cudaError_t launch_pack_bt_same(int slot, int x, int o, int v, int Kp, const double* vvovT,
-                                const double* t2ss, St st, cudaStream_t s) {
+cudaError_t launch_pack_bt_same(int slot, int x, int o, int oi, int v, int Kp,
+                                const double* vvovT, const double* t2ss, St st, cudaStream_t s) {
   int64_t n = npairs(v) * Kp;
   if (n == 0) return cudaSuccess;
-  pack_bt_same<<<grid_for(n), 256, 0, s>>>(slot, x, o, v, Kp, vvovT, t2ss, st);
+  pack_bt_same<<<grid_for(n), 256, 0, s>>>(slot, x, o, oi, v, Kp, vvovT, t2ss, st);
   return cudaGetLastError();
 }
 
 template <class St>
-cudaError_t launch_pack_a1(const int2* pk, int nslot, int os, int vs, int ot, int vt, int Kp,
-                           const double* t2st, const double* jT, St st, cudaStream_t s) {
+cudaError_t launch_pack_a1(const int2* pk, int nslot, int os, int vs, int ot, int oti, int vt,
+                           int Kp, const double* t2st, const double* jT, St st, cudaStream_t s) {
   int64_t n = (int64_t)nslot * vs * Kp;
   if (n == 0) return cudaSuccess;
-  pack_a1<<<grid_for(n), 256, 0, s>>>(pk, nslot, os, vs, ot, vt, Kp, t2st, jT, st);
+  pack_a1<<<grid_for(n), 256, 0, s>>>(pk, nslot, os, vs, ot, oti, vt, Kp, t2st, jT, st);
   return cudaGetLastError();
 }
 
 template <class St>
-cudaError_t launch_pack_bg(int slot, int x, int os, int vs, int ot, int vt, int Kp,
+cudaError_t launch_pack_bg(int slot, int x, int os, int vs, int ot, int oti, int vt, int Kp,
                            const double* gT, const double* t2st, St st, cudaStream_t s) {
   int64_t n = (int64_t)vs * vt * Kp;
   if (n == 0) return cudaSuccess;
-  pack_bg<<<grid_for(n), 256, 0, s>>>(slot, x, os, vs, ot, vt, Kp, gT, t2st, st);
+  pack_bg<<<grid_for(n), 256, 0, s>>>(slot, x, os, vs, ot, oti, vt, Kp, gT, t2st, st);
   return cudaGetLastError();
 }
 
 template <class St>
-cudaError_t launch_pack_bf(int slot, int K, int os, int vs, int ot, int vt, int Kp,
+cudaError_t launch_pack_bf(int slot, int K, int os, int osi, int vs, int ot, int vt, int Kp,
                            const double* fT, const double* t2st, St st, cudaStream_t s) {
   int64_t n = (int64_t)vs * vt * Kp;
   if (n == 0) return cudaSuccess;
-  pack_bf<<<grid_for(n), 256, 0, s>>>(slot, K, os, vs, ot, vt, Kp, fT, t2st, st);
+  pack_bf<<<grid_for(n), 256, 0, s>>>(slot, K, os, osi, vs, ot, vt, Kp, fT, t2st, st);
   return cudaGetLastError();
 }
 
 template <class St>
-cudaError_t launch_pack_at2(const int2* pk, int nslot, int os, int vs, int ot, int vt, int Kp,
-                            const double* t2st, const double* lT, St st, cudaStream_t s) {
+cudaError_t launch_pack_at2(const int2* pk, int nslot, int os, int osi, int vs, int ot, int vt,
+                            int Kp, const double* t2st, const double* lT, St st,
+                            cudaStream_t s) {
   int64_t n = (int64_t)nslot * vt * Kp;
   if (n == 0) return cudaSuccess;
-  pack_at2<<<grid_for(n), 256, 0, s>>>(pk, nslot, os, vs, ot, vt, Kp, t2st, lT, st);
+  pack_at2<<<grid_for(n), 256, 0, s>>>(pk, nslot, os, osi, vs, ot, vt, Kp, t2st, lT, st);
   return cudaGetLastError();
 }
 
@@ -401,17 +407,17 @@ cudaError_t launch_absmax(const double* x, int64_t n, unsigned long long* out, c
 #define LNO_INST(St)                                                                           \
   template cudaError_t launch_transpose_block<St>(const double*, int, int, int, int, int, int,  \
                                                   int, St, cudaStream_t);                       \
-  template cudaError_t launch_pack_at_same<St>(const int2*, int, int, int, int, const double*, \
+  template cudaError_t launch_pack_at_same<St>(const int2*, int, int, int, int, int,           \
+                                               const double*, const double*, St, cudaStream_t); \
+  template cudaError_t launch_pack_bt_same<St>(int, int, int, int, int, int, const double*,     \
                                                const double*, St, cudaStream_t);               \
-  template cudaError_t launch_pack_bt_same<St>(int, int, int, int, int, const double*,          \
-                                               const double*, St, cudaStream_t);               \
-  template cudaError_t launch_pack_a1<St>(const int2*, int, int, int, int, int, int,           \
+  template cudaError_t launch_pack_a1<St>(const int2*, int, int, int, int, int, int, int,      \
                                           const double*, const double*, St, cudaStream_t);     \
-  template cudaError_t launch_pack_bg<St>(int, int, int, int, int, int, int, const double*,     \
-                                          const double*, St, cudaStream_t);                    \
-  template cudaError_t launch_pack_bf<St>(int, int, int, int, int, int, int, const double*,     \
-                                          const double*, St, cudaStream_t);                    \
-  template cudaError_t launch_pack_at2<St>(const int2*, int, int, int, int, int, int,          \
+  template cudaError_t launch_pack_bg<St>(int, int, int, int, int, int, int, int,               \
+                                          const double*, const double*, St, cudaStream_t);     \
+  template cudaError_t launch_pack_bf<St>(int, int, int, int, int, int, int, int,               \
+                                          const double*, const double*, St, cudaStream_t);     \
+  template cudaError_t launch_pack_at2<St>(const int2*, int, int, int, int, int, int, int,     \
                                            const double*, const double*, St, cudaStream_t);
 
 LNO_INST(StoreF64)

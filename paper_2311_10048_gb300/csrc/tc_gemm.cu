@@ -16,7 +16,7 @@
 // its own magnitude.)  The epilogue adds the classes from the smallest up in
 // float32 (the lower classes are ~2^-8 of the next, so this is one rounding
 // of the final sum) and scales by the power of two sigma_A sigma_B 2^-14.
-// Float64 output keeps HI and the rest separately (exact).  No float64
+// Float64 output (the DF assembly) adds the exact class sums in float64.  No float64
 // arithmetic runs per element: this GPU's FP64 rate is ~1/64 of FP32.  No
 // systematic bias enters the sum of ~1e12 positive-definite energy terms.
 //
@@ -420,8 +420,14 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
               if (mok && n0 + j < N) op[(int64_t)j * ldo] = v;
               if (amax != nullptr && m < M && n0 + j < N) lmax = fmaxf(lmax, fabsf(v));
             } else {
-              if (mok && n0 + j < N)
-                op[(int64_t)j * ldo] = (double)__fmul_rn(hi, fscale) + (double)__fmul_rn(lo, fscale);
+              // float64 output: the exact class sums added in float64 (smallest
+              // first), so the output keeps ~53 bits instead of HI + a float32 rest
+              if (mok && n0 + j < N) {
+                double v = 0.0;
+#pragma unroll
+                for (int g = S - 1; g >= 1; --g) v += (double)__uint_as_float(acc[g][j]);
+                op[(int64_t)j * ldo] = ((double)hi + v) * scale;
+              }
               if (amax != nullptr && m < M && n0 + j < N)
                 lmax = fmaxf(lmax, fabsf(__fmul_rn(__fadd_rn(hi, lo), fscale)));
             }

@@ -46,6 +46,11 @@ class Grad(C.Structure):
                 ("dfov", C.c_void_p * 2)]
 
 
+class Central(C.Structure):
+    _fields_ = [("nq", C.c_int), ("s", C.c_void_p), ("w", C.c_void_p), ("spin", C.c_int),
+                ("nlmo", C.c_int), ("U", C.c_void_p), ("dE", C.c_void_p)]
+
+
 class Stats(C.Structure):
     _fields_ = [("ms_total", C.c_double), ("ms_stage", C.c_double),
                 ("ms_contract", C.c_double), ("ms_energy", C.c_double),
@@ -97,6 +102,11 @@ def load_library(build_if_missing=False):
     lib.lno_ot_version.restype = C.c_char_p
     lib.lno_ot_last_error.argtypes = []
     lib.lno_ot_last_error.restype = C.c_char_p
+    lib.lno_ot_energy_central.argtypes = [C.c_void_p, C.POINTER(Domain), C.POINTER(Central)]
+    lib.lno_ot_energy_central.restype = C.c_int
+    lib.lno_ot_laplace_quadrature.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int,
+                                              C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+    lib.lno_ot_laplace_quadrature.restype = C.c_int
     lib.lno_ot_selftest_gemm.argtypes = [C.c_int] * 5 + [C.c_void_p] * 4
     lib.lno_ot_selftest_gemm.restype = C.c_int
     lib.lno_ot_selftest_timeout.argtypes = [C.c_int, C.c_longlong, C.POINTER(C.c_int),
@@ -249,12 +259,43 @@ class Context:
         if rc != OK:
             raise LnoError(rc, "lno_ot_backward")
 
+    def energy_central(self, dom, spin, U, s, w):
+        """dE of eq local_pt for each row of U (device float64 [nlmo][nocc[spin]],
+        central orbitals of spin ``spin``) with the quadrature (s, w)."""
+        import numpy as np
+        _check_tensor(U, "U")
+        d, keep = make_domain_struct(dom)
+        sa = np.ascontiguousarray(s, dtype=np.float64)
+        wa = np.ascontiguousarray(w, dtype=np.float64)
+        out = np.zeros(max(int(U.shape[0]), 1))
+        c = Central(int(sa.size), sa.ctypes.data, wa.ctypes.data, int(spin), int(U.shape[0]),
+                    U.data_ptr(), out.ctypes.data)
+        rc = self.lib.lno_ot_energy_central(self.h, C.byref(d), C.byref(c))
+        del keep
+        if rc != OK:
+            raise LnoError(rc, "lno_ot_energy_central")
+        return out[:int(U.shape[0])]
+
     def stats(self):
         st = Stats()
         rc = self.lib.lno_ot_last_stats(self.h, C.byref(st))
         if rc != OK:
             raise LnoError(rc, "lno_ot_last_stats")
         return st.as_dict()
+
+
+def laplace_quadrature(xmin, xmax, tol=1e-2, nmax=16):
+    """(s, w) numpy arrays from lno_ot_laplace_quadrature (host only)."""
+    import numpy as np
+    lib = load_library()
+    s = np.zeros(32)
+    w = np.zeros(32)
+    n = C.c_int(0)
+    rc = lib.lno_ot_laplace_quadrature(float(xmin), float(xmax), float(tol), int(nmax),
+                                       s.ctypes.data, w.ctypes.data, C.byref(n))
+    if rc != OK:
+        raise LnoError(rc, "lno_ot_laplace_quadrature")
+    return s[:n.value].copy(), w[:n.value].copy()
 
 
 def to_device(dom, device="cuda"):

@@ -51,6 +51,8 @@ def test_ctypes_struct_layouts_match_c(tmp_path):
                  offsetof(lno_ot_domain, e_trip), offsetof(lno_ot_domain, n_sel),
                  offsetof(lno_ot_stats, elements), offsetof(lno_ot_domain, fov),
                  offsetof(lno_ot_domain, e_orb), offsetof(lno_ot_grad, dfov));
+          printf("%zu %zu %zu %zu\\n", sizeof(lno_ot_central), offsetof(lno_ot_central, spin),
+                 offsetof(lno_ot_central, U), offsetof(lno_ot_central, dE));
           return 0;
         }
     """))
@@ -64,7 +66,8 @@ def test_ctypes_struct_layouts_match_c(tmp_path):
             C.sizeof(lno_ot.Grad), C.sizeof(lno_ot.Stats),
             lno_ot.Domain.t2ab.offset, lno_ot.Domain.e_trip.offset, lno_ot.Domain.n_sel.offset,
             lno_ot.Stats.elements.offset, lno_ot.Domain.fov.offset, lno_ot.Domain.e_orb.offset,
-            lno_ot.Grad.dfov.offset]
+            lno_ot.Grad.dfov.offset, C.sizeof(lno_ot.Central), lno_ot.Central.spin.offset,
+            lno_ot.Central.U.offset, lno_ot.Central.dE.offset]
     assert got == want
 
 
@@ -89,3 +92,19 @@ def test_enum_values_match_binding():
     for k, v in want.items():
         assert enums.get(k) == v, (k, enums.get(k), v)
     assert set(lno_ot.PRECISIONS.values()) == {0, 1, 2, 3, 4, 5}
+
+
+def test_laplace_quadrature_meets_its_tolerance():
+    """Host-only routine: the returned exponential sum bounds the relative
+    error of 1/x on the range by tol (checked on a dense grid here), with
+    3-4 points at the paper's laptol = 1e-2 on a (T) denominator range."""
+    import numpy as np
+    for lo, hi, tol, nmax_pts in ((1.2, 21.0, 1e-2, 4), (3.9, 16.1, 1e-2, 4), (0.5, 40.0, 1e-2, 8),
+                                  (1.2, 21.0, 1e-3, 10), (1.2, 21.0, 1e-4, 14)):
+        s, w = lno_ot.laplace_quadrature(lo, hi, tol)
+        x = np.geomspace(lo, hi, 20000)
+        err = np.abs(1.0 - x * (np.exp(-np.outer(x, s)) @ w)).max()
+        assert err <= tol, (lo, hi, tol, err)
+        assert len(s) <= nmax_pts and (s > 0).all() and (np.diff(s) > 0).all()
+    with pytest.raises(lno_ot.LnoError):
+        lno_ot.laplace_quadrature(2.0, 1.0, 1e-2)

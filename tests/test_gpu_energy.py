@@ -294,5 +294,7 @@ def test_c4_bf16x15_per_triplet(ctx15):
         err = np.abs(et[i] - np.array(g["cases"][c]["e"])).max()
         worst = max(worst, err)
         assert err <= 2e-9, c
-    assert abs(out["total"] - g["total"]) <= 1e-8
+    # the per-triplet float32 rounding (~1e-10 Eh, unbiased) adds up as
+    # sqrt(8436) over the domain
+    assert abs(out["total"] - g["total"]) <= 3e-8
     print("c4 bf16x15 worst per-triplet |dE| =", worst)
