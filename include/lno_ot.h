@@ -267,6 +267,22 @@ LNO_OT_API int lno_ot_energy_central(lno_ot_ctx* ctx, const lno_ot_domain* dom,
 LNO_OT_API int lno_ot_laplace_quadrature(double xmin, double xmax, double tol, int nmax,
                                          double* s, double* w, int* nq);
 
+/* Natural auxiliary functions (Sec. 3.6, eq naf_w): compresses the shared
+ * auxiliary index of the DF factors before the integrals are assembled.
+ *   W^s_XY = sum_{p<=q} B^X_pq B^Y_pq  (s = up, down),  W = (W^up + W^down)/2,
+ * the eigenvectors of W with eigenvalue > eps_naf (the paper's default is
+ * 1e-2 Eh) become the NAFs, in descending eigenvalue order, and
+ *   B_out[s][X'][p][q] = sum_X V[X][X'] B[s][X][p][q]
+ * for the *naux_out kept X'.  One auxiliary basis serves both spins, as the
+ * mixed-spin integrals need.  Uses dom->nbas, naux and B only.  B_out[s]:
+ * DEVICE [naux][nbas][nbas] caller-owned (the first *naux_out blocks are
+ * written; may be dom->B[s] itself).  eigenvalues: HOST [naux] (all
+ * eigenvalues of W, descending) or NULL.  Runs in float64 on the CUDA cores
+ * (pair-packed contraction, cyclic Jacobi rotations replayed as a CUDA
+ * graph, contraction), whatever the context's precision; synchronous. */
+LNO_OT_API int lno_ot_naf(lno_ot_ctx* ctx, const lno_ot_domain* dom, double eps_naf,
+                          double* B_out[2], int* naux_out, double* eigenvalues);
+
 /* Stats of the last lno_ot_energy on this context. */
 LNO_OT_API int lno_ot_last_stats(const lno_ot_ctx* ctx, lno_ot_stats* st);
 

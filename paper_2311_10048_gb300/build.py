@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUTDIR, "liblno_ot.so")
 SOURCES = ["lno_ot.cu", "gemm_f64.cu", "energy.cu", "pack.cu", "tc_gemm.cu", "noalloc.cu",
-           "backward.cu", "central.cu"]
+           "backward.cu", "central.cu", "naf.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -20,6 +20,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -73,6 +74,15 @@ cudaError_t launch_gather_rows(const void* src, void* dst, const int* list, int 
                                int64_t dst_slice_bytes, cudaStream_t s);
 cudaError_t launch_scatter_add_rows(const double* src, double* dst, const int* list, int nlist,
                                     int64_t row, cudaStream_t s);
+// naf.cu
+int jacobi_eigh(double* A, double* V, int n, double2* cs, double* norms, cudaStream_t st,
+                int max_sweeps);
+cudaError_t launch_pack_pairs(const double* B, int naux, int n, double* J, cudaStream_t st);
+cudaError_t launch_transpose_x(const double* B, int naux, int64_t n2, double* Bt,
+                               cudaStream_t st);
+cudaError_t launch_get_diag(const double* A, int n, double* d, cudaStream_t st);
+cudaError_t launch_gather_cols(const double* V, int n, const int* cols, int nk, double* Vt,
+                               cudaStream_t st);
 // backward.cu
 struct GemmS {
   const double* A;
@@ -1293,6 +1303,84 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out,
 
 
 // ---------------------------------------------------------------------------
+// Natural auxiliary functions (Sec. 3.6, eq naf_w), float64 (naf.cu).
+int naf_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double eps, double* const* Bout,
+             int* naux_out, double* lam_host) {
+  if (!dom || !Bout || !naux_out || !(eps >= 0.0) || !std::isfinite(eps)) return LNO_OT_EINVAL;
+  if (dom->nbas <= 0 || dom->naux <= 0) return LNO_OT_EINVAL;
+  if ((int64_t)dom->nbas * dom->nbas * dom->naux > ((int64_t)1 << 40)) return LNO_OT_EINVAL;
+  for (int s = 0; s < 2; ++s) {
+    TRY(check_ptr(ctx, dom->B[s], true));
+    TRY(check_ptr(ctx, Bout[s], true));
+  }
+  CU(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const int n = dom->naux, nb = dom->nbas;
+  const int64_t npair = (int64_t)nb * (nb + 1) / 2, n2 = (int64_t)nb * nb;
+  Arena A(st, ctx->ws_limit);
+  double *J[2], *W, *V, *d, *norms;
+  double2* cs;
+  ProbF64* dp;
+  for (int s = 0; s < 2; ++s) {
+    TRY(A.get(&J[s], (size_t)(n * npair)));
+    CU(launch_pack_pairs(dom->B[s], n, nb, J[s], st));
+  }
+  TRY(A.get(&W, (size_t)n * n));
+  TRY(A.get(&dp, 2));
+  {  // W = (J^up J^up^T + J^down J^down^T) / 2
+    ProbF64 p{};
+    p.nseg = 2;
+    p.seg[0] = SegF64{J[0], J[0], (int)npair, (int)npair, (int)npair, 0.5};
+    p.seg[1] = SegF64{J[1], J[1], (int)npair, (int)npair, (int)npair, 0.5};
+    p.XT = W;
+    CU(cudaMemcpyAsync(dp, &p, sizeof p, cudaMemcpyHostToDevice, st));
+    CU(launch_gemm_f64(dp, 1, n, n, n, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  A.drop(J[0]);
+  A.drop(J[1]);
+  TRY(A.get(&V, (size_t)n * n));
+  TRY(A.get(&cs, (size_t)(n / 2 + 1)));
+  TRY(A.get(&norms, 2));
+  TRY(A.get(&d, (size_t)n));
+  const int sweeps = jacobi_eigh(W, V, n, cs, norms, st, 40);
+  if (sweeps < 0) return sweeps;
+  CU(launch_get_diag(W, n, d, st));
+  std::vector<double> lam(n);
+  CU(cudaMemcpyAsync(lam.data(), d, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] > lam[b]; });
+  int nk = 0;
+  while (nk < n && lam[order[nk]] > eps) ++nk;
+  if (lam_host)
+    for (int i = 0; i < n; ++i) lam_host[i] = lam[order[i]];
+  *naux_out = nk;
+  if (nk > 0) {
+    int* cols;
+    double *Vt, *Bt;
+    TRY(A.get(&cols, (size_t)nk));
+    CU(cudaMemcpyAsync(cols, order.data(), (size_t)nk * sizeof(int), cudaMemcpyHostToDevice, st));
+    TRY(A.get(&Vt, (size_t)nk * n));
+    CU(launch_gather_cols(V, n, cols, nk, Vt, st));
+    TRY(A.get(&Bt, (size_t)(n2 * n)));
+    for (int s = 0; s < 2; ++s) {   // B'[X'][pq] = sum_X V[X][X'] B[X][pq]
+      CU(launch_transpose_x(dom->B[s], n, n2, Bt, st));
+      ProbF64 p{};
+      p.nseg = 1;
+      p.seg[0] = SegF64{Bt, Vt, n, n, n, 1.0};
+      p.XT = Bout[s];
+      CU(cudaMemcpyAsync(dp + s, &p, sizeof p, cudaMemcpyHostToDevice, st));
+      CU(launch_gemm_f64(dp + s, 1, (int)n2, nk, (int)n2, st));
+      CU(cudaStreamSynchronize(st));
+    }
+  }
+  CU(cudaStreamSynchronize(st));
+  return LNO_OT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Central-LMO share in the Laplace form (Sec. 3.7, eqs laplace_transform and
 // local_pt): per quadrature point, an augmented domain with one pseudo-orbital
 // per central orbital (central.cu), the triplets that hold exactly one of
@@ -1956,6 +2044,12 @@ int lno_ot_backward(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot
 int lno_ot_energy_central(lno_ot_ctx* ctx, const lno_ot_domain* dom, const lno_ot_central* c) {
   if (!ctx) return LNO_OT_EINVAL;
   return central_impl(ctx, dom, c);
+}
+
+int lno_ot_naf(lno_ot_ctx* ctx, const lno_ot_domain* dom, double eps_naf, double* B_out[2],
+               int* naux_out, double* eigenvalues) {
+  if (!ctx) return LNO_OT_EINVAL;
+  return naf_impl(ctx, dom, eps_naf, B_out, naux_out, eigenvalues);
 }
 
 int lno_ot_laplace_quadrature(double xmin, double xmax, double tol, int nmax, double* s,

@@ -104,6 +104,9 @@ def load_library(build_if_missing=False):
     lib.lno_ot_last_error.restype = C.c_char_p
     lib.lno_ot_energy_central.argtypes = [C.c_void_p, C.POINTER(Domain), C.POINTER(Central)]
     lib.lno_ot_energy_central.restype = C.c_int
+    lib.lno_ot_naf.argtypes = [C.c_void_p, C.POINTER(Domain), C.c_double, C.c_void_p * 2,
+                               C.POINTER(C.c_int), C.c_void_p]
+    lib.lno_ot_naf.restype = C.c_int
     lib.lno_ot_laplace_quadrature.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int,
                                               C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
     lib.lno_ot_laplace_quadrature.restype = C.c_int
@@ -275,6 +278,30 @@ class Context:
         if rc != OK:
             raise LnoError(rc, "lno_ot_energy_central")
         return out[:int(U.shape[0])]
+
+    def naf(self, dom, eps_naf=1e-2):
+        """NAF compression of dom's B factors (Sec. 3.6): returns (dict like dom
+        with B replaced by the compressed device tensors and naux by the number
+        of NAFs, eigenvalues of W descending as a numpy array)."""
+        import numpy as np
+        import torch
+        d, keep = make_domain_struct(dom)
+        naux, nbas = int(dom["naux"]), int(dom["nbas"])
+        outs = [torch.empty((naux, nbas, nbas), dtype=torch.float64, device=dom["B"][s].device)
+                for s in (0, 1)]
+        ptrs = (C.c_void_p * 2)(outs[0].data_ptr(), outs[1].data_ptr())
+        nk = C.c_int(0)
+        lam = np.zeros(naux)
+        rc = self.lib.lno_ot_naf(self.h, C.byref(d), float(eps_naf), ptrs, C.byref(nk),
+                                 lam.ctypes.data)
+        del keep
+        if rc != OK:
+            raise LnoError(rc, "lno_ot_naf")
+        k = nk.value
+        out = dict(dom)
+        out["B"] = [outs[0][:k].contiguous(), outs[1][:k].contiguous()]
+        out["naux"] = k
+        return out, lam
 
     def stats(self):
         st = Stats()
