@@ -413,6 +413,101 @@ def run_backward(args):
     return 0
 
 
+def run_central(args):
+    """Central-LMO share in the Laplace form (Sec. 3.7): one seeded random
+    central orbital of each spin of the domain, the laptol = 1e-2 quadrature
+    from the library; times lno_ot_energy_central (all stages, per call)."""
+    import torch
+    from paper_2311_10048_gb300 import lno_ot
+    cfg = dict(CONFIGS[args.config])
+    dom = make_domain(**cfg)
+    nbas, nocc = dom["nbas"], dom["nocc"]
+    dev = torch.device("cuda", 0)
+    dd = lno_ot.to_device(dom, dev)
+    eo = np.sort(np.concatenate([dom["eps"][0][:nocc[0]], dom["eps"][1][:nocc[1]]]))
+    ev = np.sort(np.concatenate([dom["eps"][0][nocc[0]:], dom["eps"][1][nocc[1]:]]))
+    lo, hi = ev[:3].sum() - eo[-3:].sum(), ev[-3:].sum() - eo[:3].sum()
+    s, w = lno_ot.laplace_quadrature(lo, hi, 1e-2)
+    rng = np.random.default_rng(17)
+    U = []
+    for x in (0, 1):
+        u = rng.standard_normal((1, nocc[x]))
+        U.append(torch.as_tensor(u / np.linalg.norm(u), dtype=torch.float64, device=dev))
+    ctx = lno_ot.Context(0, args.precision)
+    for _ in range(args.warmup if args.warmup < 3 else 1):
+        ctx.energy_central(dd, 0, U[0], s, w)
+    torch.cuda.synchronize()
+    res, secs, stats = [], [], []
+    for x in (0, 1):
+        t0 = time.perf_counter()
+        res.append(float(ctx.energy_central(dd, x, U[x], s, w)[0]))
+        secs.append(time.perf_counter() - t0)
+        stats.append(ctx.stats())
+    ctx.close()
+    na, nb = nocc
+    c2 = lambda n: n * (n - 1) // 2
+    # triplets per central orbital and quadrature point: same-spin pairs,
+    # same-spin x other-spin, other-spin pairs
+    fl = 0.0
+    for x, (o, ot) in enumerate(((na, nb), (nb, na))):
+        cs = ("aaa", "aab", "abb") if x == 0 else ("bbb", "abb", "aab")
+        fl += len(s) * (c2(o) * alg_flops_triplet(cs[0], nocc, nbas)
+                        + o * ot * alg_flops_triplet(cs[1], nocc, nbas)
+                        + c2(ot) * alg_flops_triplet(cs[2], nocc, nbas))
+    line = {"metric": "central-LMO (T) share, Laplace form (eq local_pt): TFLOP/s",
+            "value": fl / sum(secs) / 1e12, "unit": UNIT, "higher_is_better": True,
+            "dtype": "bf16" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.config) + "; one random central orbital "
+                                                               "per spin", **cfg_public(cfg)},
+            "quadrature": {"points": len(s), "laptol": 1e-2, "range_Eh": [lo, hi],
+                           "s": s.tolist(), "w": w.tolist()},
+            "dE_Eh": {"spin_up": res[0], "spin_down": res[1]},
+            "seconds": {"spin_up": secs[0], "spin_down": secs[1]},
+            "breakdown_ms": [{k: st[k] for k in ("ms_total", "ms_stage", "ms_contract",
+                                                 "ms_energy")} for st in stats],
+            "precision": args.precision}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_naf(args):
+    """NAF compression (Sec. 3.6): time lno_ot_naf at eps_naf = 1e-2 and at a
+    threshold that keeps about half of the auxiliary functions, and the E(T)
+    change of the compressed domain (timed precision)."""
+    import torch
+    from paper_2311_10048_gb300 import lno_ot
+    cfg = dict(CONFIGS[args.config])
+    dom = make_domain(**cfg)
+    dd = lno_ot.to_device(dom, torch.device("cuda", 0))
+    c64 = lno_ot.Context(0, "fp64")
+    c64.naf(dd, 1e-2)      # warm-up
+    torch.cuda.synchronize()
+    out = {}
+    t0 = time.perf_counter()
+    comp, lam = c64.naf(dd, 1e-2)
+    out["1e-2"] = {"seconds": time.perf_counter() - t0, "naux_kept": comp["naux"]}
+    eps_half = float(lam[len(lam) // 2])
+    t0 = time.perf_counter()
+    comp_h, _ = c64.naf(dd, eps_half)
+    out["half"] = {"eps_naf": eps_half, "seconds": time.perf_counter() - t0,
+                   "naux_kept": comp_h["naux"]}
+    c64.close()
+    del comp
+    ctx = lno_ot.Context(0, args.precision)
+    e_full = ctx.energy(dd)["total"]
+    e_half = ctx.energy(comp_h)["total"]
+    ctx.close()
+    line = {"metric": "NAF compression (eq naf_w) seconds and E(T) change", "unit": "s",
+            "value": out["1e-2"]["seconds"], "higher_is_better": False, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.config), **cfg_public(cfg)},
+            "naux": dom["naux"], "eigenvalues": {"max": float(lam[0]), "min": float(lam[-1])},
+            "runs": out, "E_full_Eh": e_full, "E_half_naf_Eh": e_half,
+            "dE_half_Eh": e_half - e_full, "energy_precision": args.precision}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def step_blocks(nocc, K):
     """trip_sel of each of K steps: block s of every case's triplets."""
     out = []
@@ -482,7 +577,9 @@ def run_domain(args):
     if args.closed_shell:  # the closed-shell calling form: one set of arrays for both spins
         dd = dict(dd, B=[dd["B"][0]] * 2, eps=[dd["eps"][0]] * 2, t1=[dd["t1"][0]] * 2,
                   t2bb=dd["t2aa"])
-    ctx = lno_ot.Context(local, args.precision)
+    # the context keeps the domain's DF blocks and contraction operands
+    # between the steps (built once, for all triplets, by the first step)
+    ctx = lno_ot.Context(local, args.precision, keep_operands=not args.no_keep)
     alg = total_alg_flops(nocc, nbas)
     # per-triplet contributions of the whole domain, written block by block
     et = [torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in ntr]
@@ -501,6 +598,9 @@ def run_domain(args):
 
     for w in range(args.warmup):
         step(w)
+    # the timed region builds the operands again: nothing prepared by the
+    # warm-up is reused
+    ctx.release()
     torch.cuda.synchronize()
 
     # timed region: K steps = the whole domain once, device-resident inputs
@@ -570,7 +670,9 @@ def run_domain(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 40,
                "steps": args.e2e_steps, "seconds_per_step": e2e_s,
                "what": "lno_ot_energy on one step's triplet block; every step copies the whole "
-                       "domain's inputs from pinned host memory and reads the 5 energies back"}
+                       "domain's inputs from pinned host memory (new device arrays, so the "
+                       "step also stages them and builds all operands) and reads the 5 "
+                       "energies back"}
     ctx.close()
 
     # plain FP64 GPU path on a seeded triplet sample (same domain, same GPU)
@@ -657,7 +759,9 @@ def run_domain(args):
                                 else workload_name(args.config))
                    + (" + f_ov (RO reference)" if args.fov else "")
                    + f"; the {K} timed steps compute the whole domain once (step s: block s "
-                     f"of {K} of every spin case's restricted triplets, all stages of the path)",
+                     f"of {K} of every spin case's restricted triplets; the first step also "
+                     f"stages the domain and builds its DF blocks and contraction operands, "
+                     f"which the context keeps for the later steps)",
                    **cfg_public(cfg), **({"fov_sd": 0.02} if args.fov else {}),
                    "triplets": dict(zip(CASES, ntr)),
                    "l2": f"inputs larger than L2 ({domain_bytes(nbas, nocc, dom['naux']) / 1e9:.1f} GB)",
@@ -707,19 +811,24 @@ def main():
     ap.add_argument("--backward", action="store_true", help="time the adjoint on a sample")
     ap.add_argument("--bwd-sample", type=int, default=1, help="adjoint triplets per case")
     ap.add_argument("--precision", default="bf16x10",
-                    choices=["bf16x15", "bf16x10", "bf16x6", "bf16x3"])
+                    choices=["bf16x15", "bf16x10", "bf16x6", "bf16x3", "fp64"])
     ap.add_argument("--ref-precision", default="bf16x15", choices=["bf16x15", "none"],
                     help="whole-domain reference run that measures the domain-total error")
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle triplets per case")
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--fp64-sample", type=int, default=32, help="FP64-path triplets per case")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-keep", action="store_true",
+                    help="every step builds its own operands (no keep_operands)")
     ap.add_argument("--closed-shell", action="store_true",
                     help="closed-shell domain (nocc of spin up for both spins, identical data); "
                          "both spins passed as the same arrays, so the spin-flip images run once")
     ap.add_argument("--fov", action="store_true",
                     help="restricted open-shell domain: add an f_ov block (and time the "
                          "orbital contributions too)")
+    ap.add_argument("--central", action="store_true",
+                    help="time the central-LMO share in the Laplace form (eq local_pt)")
+    ap.add_argument("--naf", action="store_true", help="time the NAF compression (eq naf_w)")
     ap.add_argument("--shape", default=None,
                     help="custom domain nbas,nalpha,nbeta,naux (recipe of the configs, seed 5)")
     args = ap.parse_args()
@@ -735,6 +844,10 @@ def main():
         return run_c3(args)
     if args.backward:
         return run_backward(args)
+    if args.central:
+        return run_central(args)
+    if args.naf:
+        return run_naf(args)
     return run_domain(args)
 
 

@@ -98,6 +98,18 @@ typedef struct {
                              on triplets per contraction launch.  Lines
                              starting with '#' are comments.  Unreadable
                              file: lno_ot_init returns LNO_OT_EINVAL. */
+  int keep_operands;      /* 0: every lno_ot_energy call builds and frees its
+                             own DF blocks and contraction operands.  1: the
+                             context keeps those of the last domain, built for
+                             ALL its triplets, and a later lno_ot_energy on the
+                             same arrays (same pointers, sizes and precision;
+                             e.g. another trip_sel block) only runs the
+                             contractions and the energy kernels.  The caller
+                             must not change the arrays' contents while they
+                             are kept (lno_ot_release frees them).  Costs the
+                             whole domain's operands in device memory; if they
+                             do not fit the call runs uncached.  Closed-shell
+                             calls (spin-flip images) are never cached. */
 } lno_ot_options;
 
 /* One domain.  Orbitals of each spin are ordered occupied first (ascending
@@ -208,6 +220,10 @@ LNO_OT_API int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt);
 /* Release the context and its device buffers (after its stream drained). */
 LNO_OT_API void lno_ot_destroy(lno_ot_ctx* ctx);
 
+/* Free the operands kept by options.keep_operands (no-op when none are
+ * kept); the next lno_ot_energy builds them again. */
+LNO_OT_API int lno_ot_release(lno_ot_ctx* ctx);
+
 /* E(T) of one domain (eq cim_pt_energy, all occupied orbitals of the
  * domain).  out: host memory; out->status mirrors the return value. */
 LNO_OT_API int lno_ot_energy(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out);
@@ -244,7 +260,7 @@ LNO_OT_API int lno_ot_backward(lno_ot_ctx* ctx, const lno_ot_domain* dom, double
  * domain's trip_sel, e_trip and e_orb members are ignored.  Runs in the
  * context's precision; results in host memory on return. */
 typedef struct {
-  int nq;                 /* quadrature points, 1..32 */
+  int nq;                 /* quadrature points, 1..256 */
   const double* s;        /* HOST [nq] points s_q > 0 (1/Eh) */
   const double* w;        /* HOST [nq] weights w_q */
   int spin;               /* 0: central orbitals of spin up, 1: spin down */

@@ -353,9 +353,13 @@ __device__ __forceinline__ float div_nr(float num, float D) {
   return __fmul_rn(num, r);
 }
 
-// Laplace weight -w exp(s D) of one element (D < 0, so the argument is <= 0).
-__device__ __forceinline__ float lap_weight(float nw, float s, float D) {
-  return __fmul_rn(nw, expf(__fmul_rn(s, D)));
+// Laplace factor exp(s D) of one element (D < 0, so the argument is <= 0),
+// with s carried as a float pair (s_hi + s_lo): rounding s to one float would
+// shift every factor by the same relative amount, a bias; the quadrature
+// weight -w is applied to the float64 partial sums instead, for the same
+// reason.
+__device__ __forceinline__ float lap_factor(float shi, float slo, float D) {
+  return expf(__fmaf_rn(shi, D, __fmul_rn(slo, D)));
 }
 
 // Energy of float32 X with register prefetch of the next cube tile.
@@ -410,7 +414,8 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   const int nvs = a.nvs, nvt = a.nvt;
   const TwoF eocc = split_df(MIXED ? a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_t[tr.k]
                                    : a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_s[tr.k]);
-  const float lnw = (float)(-a.lap_w), ls = (float)a.lap_s;   // Laplace weight (LAP only)
+  const float lshi = (float)a.lap_s;                          // Laplace s (LAP only)
+  const float lslo = (float)(a.lap_s - (double)lshi);
 
   float4 xr[3][4];
   float vr[9];
@@ -643,7 +648,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
               float s, e;
               two_sum(dbc[sb].hi, -da.w, s, e);
               const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc[sb].lo, del)));
-              const float qv = LAP ? __fmul_rn(num, lap_weight(lnw, ls, D)) : div_nr(num, D);
+              const float qv = LAP ? __fmul_rn(num, lap_factor(lshi, lslo, D)) : div_nr(num, D);
               part = __fadd_rn(part, valid ? qv : 0.f);
             }
           }
@@ -683,7 +688,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
                   float s, e;
                   two_sum(dbc[sb].hi, -da.w, s, e);
                   const float D = __fadd_rn(s, __fadd_rn(e, __fsub_rn(dbc[sb].lo, del)));
-                  part = __fadd_rn(part, LAP ? __fmul_rn(num, lap_weight(lnw, ls, D))
+                  part = __fadd_rn(part, LAP ? __fmul_rn(num, lap_factor(lshi, lslo, D))
                                              : div_nr(num, D));
                 }
               }
@@ -707,7 +712,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   if (tid == 0) {
     double sum = 0.0;
     for (int w = 0; w < 8; ++w) sum += red[w];
-    a.partial[(int64_t)g * gridDim.x + blockIdx.x] = sum;
+    a.partial[(int64_t)g * gridDim.x + blockIdx.x] = LAP ? -a.lap_w * sum : sum;
   }
 }
 

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -158,7 +159,12 @@ struct lno_ot_ctx {
   lno_ot_stats stats{};
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
+  // prepared operands of the last domain (options.keep_operands)
+  bool keep = false;
+  struct DomainCache* cache = nullptr;
 };
+
+void destroy_cache(DomainCache* c);
 
 namespace {
 
@@ -856,6 +862,10 @@ struct SpinPass {
     }
     int G = (int)std::max<int64_t>(
         1, std::min<int64_t>(group_cap, budget / std::max<int64_t>(per_trip, 1)));
+    // energy chunks per triplet from the domain's shape only, so that a
+    // triplet's partial sums (and its e_t, bit for bit) do not depend on
+    // which other triplets the call selects
+    const int Gshape = G;
     G = std::min(G, ntrip);
     char *X = nullptr, *Z = nullptr;
     TRY(A.get(&X, (size_t)(G * N1 * P1 * esz) + 64));
@@ -887,7 +897,7 @@ struct SpinPass {
     CU(cudaMemcpyAsync(dtrips, cs.trips.data(), ntrip * sizeof(Trip), cudaMemcpyHostToDevice,
                        R.st));
     const int target = R.ctx->nsm * 6;
-    const int P = std::max(1, std::min((int)blocks.size(), target / G + 1));
+    const int P = std::max(1, std::min((int)blocks.size(), target / Gshape + 1));
     const bool fov = R.fov[0] != nullptr;   // restricted open-shell f_ov term
     double* partial;
     TRY(A.get(&partial, (size_t)G * P * (fov ? 2 : 1)));
@@ -1080,15 +1090,23 @@ struct SpinPass {
     return LNO_OT_OK;
   }
 
-  int run() {
-    if (same.trips.empty() && mixed.trips.empty()) return LNO_OT_OK;
+  // operands for the current selections (the whole domain when cached)
+  int prepare() {
     plan();
     TRY(prepare_inputs());
     TRY(build_v_blocks());
     TRY(build());
+    return LNO_OT_OK;
+  }
+  int compute() {
     TRY(run_case(false));
     TRY(run_case(true));
     return LNO_OT_OK;
+  }
+  int run() {
+    if (same.trips.empty() && mixed.trips.empty()) return LNO_OT_OK;
+    TRY(prepare());
+    return compute();
   }
 };
 
@@ -1129,114 +1147,11 @@ int validate(const lno_ot_ctx* ctx, const lno_ot_domain* d) {
   return LNO_OT_OK;
 }
 
-// Settings of an internal energy pass over an augmented domain (the central
-// LMOs of the Laplace form): explicit triplet lists, per-spin orbital counts,
-// internal occupied ranges, one quadrature point and eq local_pt's partition.
-struct PassSpec {
-  const CaseSel* cs;   // [4]
-  int nbs[2];
-  int noi[2];
-  double lap_s, lap_w;
-};
-
-int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out,
-                const PassSpec* spec = nullptr) {
-  if (!spec) TRY(validate(ctx, dom));
-  if (ctx->prec == LNO_OT_TF32) return LNO_OT_EUNSUPPORTED;
-  CU(cudaSetDevice(ctx->device));
-  if (!spec) ctx->stats = lno_ot_stats{};
-  ctx->ev_used = 0;
-  Run R(ctx, dom);
-  if (spec) {
-    for (int s = 0; s < 2; ++s) {
-      R.nbs[s] = spec->nbs[s];
-      R.noi[s] = spec->noi[s];
-    }
-    R.lap_s = spec->lap_s;
-    R.lap_w = spec->lap_w;
-  }
-  R.f64 = ctx->prec == LNO_OT_FP64;
-  R.S = ctx->prec == LNO_OT_BF16X6    ? 3
-        : ctx->prec == LNO_OT_BF16X10 ? 4
-        : ctx->prec == LNO_OT_BF16X15 ? 5
-                                      : 2;
-  R.Sdf = ctx->prec == LNO_OT_BF16X15 ? 5 : 4;
-  CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
-  cudaEvent_t t0 = R.event(), t1 = R.event(), t2 = R.event();
-  if (t0) cudaEventRecord(t0, R.st);
-
-  CaseSel cs[4];
-  for (int c = 0; c < 4; ++c) {
-    if (spec)
-      cs[c] = spec->cs[c];
-    else
-      TRY(select_case(dom, c, cs[c]));
-  }
-  double* e_int[4];
-  for (int c = 0; c < 4; ++c)
-    TRY(R.arena.get(&e_int[c], std::max<size_t>(cs[c].trips.size(), 1)));
-  // Closed-shell domain (both spins given by the same arrays, spin-flip
-  // symmetric mixed amplitudes): bbb and abb are the spin-flip images of aaa
-  // and aab, with identical values, so only the spin-up pass runs.
-  bool flip = dom->nocc[0] == dom->nocc[1] && dom->B[0] == dom->B[1] &&
-              dom->eps[0] == dom->eps[1] && dom->t1[0] == dom->t1[1] &&
-              dom->t2aa == dom->t2bb && dom->fov[0] == dom->fov[1];
-  for (int c = 0; c < 4; ++c) flip = flip && dom->trip_sel[c] == nullptr;
-  flip = flip && spec == nullptr;
-  if (flip && dom->nocc[0] > 0 && dom->nocc[0] < dom->nbas) {
-    // symmetric to within 1e-12 of the largest amplitude: amplitudes from a
-    // closed-shell calculation agree with their spin-flip images to rounding
-    const int n = dom->nocc[0], v = dom->nbas - dom->nocc[0];
-    CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), R.st));
-    CU(launch_absmax(dom->t2ab, (int64_t)n * n * v * v, ctx->d_amax, R.st));
-    unsigned long long hm = 0;
-    CU(cudaMemcpyAsync(&hm, ctx->d_amax, sizeof hm, cudaMemcpyDeviceToHost, R.st));
-    CU(cudaStreamSynchronize(R.st));
-    double amax;
-    std::memcpy(&amax, &hm, 8);
-    unsigned int* cnt;
-    TRY(R.arena.get(&cnt, 1));
-    CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), R.st));
-    CU(launch_t2ab_flip_mismatch(dom->t2ab, n, v, 1e-12 * amax, cnt, R.st));
-    unsigned int h = 1;
-    CU(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, R.st));
-    CU(cudaStreamSynchronize(R.st));
-    R.stats->other_launches += 2;
-    flip = h == 0;
-  }
-  TRY(R.stage());
-  {
-    SpinPass pa(R, 0, cs[0], cs[1], e_int[0], e_int[1]);
-    SpinPass pb(R, 1, cs[3], cs[2], e_int[3], e_int[2]);
-    if (!R.f64) {  // integral scale: first pass over every DF block both spins need
-      pa.plan();
-      if (!flip) pb.plan();
-      TRY(pa.prepare_inputs());
-      if (!flip) TRY(pb.prepare_inputs());
-      CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), R.st));
-      TRY(pa.measure());
-      if (!flip) TRY(pb.measure());
-      unsigned long long h;
-      CU(cudaMemcpyAsync(&h, ctx->d_amax, sizeof h, cudaMemcpyDeviceToHost, R.st));
-      CU(cudaStreamSynchronize(R.st));
-      double m;
-      std::memcpy(&m, &h, 8);
-      R.sigI = pow2_scale(2.0 * m);  // antisymmetrised combinations are <= 2 max
-    }
-    if (t1) cudaEventRecord(t1, R.st);
-    TRY(pa.run());
-    pa.own.release();
-    if (!flip) {
-      TRY(pb.run());
-    } else {  // spin-flip images: bbb = aaa, abb = aab, triplet for triplet
-      if (!cs[3].trips.empty())
-        CU(cudaMemcpyAsync(e_int[3], e_int[0], cs[3].trips.size() * sizeof(double),
-                           cudaMemcpyDeviceToDevice, R.st));
-      if (!cs[2].trips.empty())
-        CU(cudaMemcpyAsync(e_int[2], e_int[1], cs[2].trips.size() * sizeof(double),
-                           cudaMemcpyDeviceToDevice, R.st));
-    }
-  }
+// Per-case sums, per-triplet and orbital outputs, results and stats of one
+// call (after the spin passes have filled e_int).
+int finish_call(lno_ot_ctx* ctx, Run& R, Arena& A, const lno_ot_domain* dom, const CaseSel* cs,
+                double* const* e_int, bool thirds, cudaEvent_t t0, cudaEvent_t t1,
+                cudaEvent_t t2, lno_ot_result* out) {
   // per-case sums
   for (int c = 0; c < 4; ++c) {
     if (cs[c].trips.empty()) {
@@ -1254,14 +1169,14 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out,
     OrbPartArgs oa{};
     oa.na = dom->nocc[0];
     oa.nb = dom->nocc[1];
-    oa.thirds = spec != nullptr;
+    oa.thirds = thirds;
     oa.out[0] = dom->e_orb[0];
     oa.out[1] = dom->e_orb[1];
     for (int c = 0; c < 4; ++c) {
       oa.e[c] = e_int[c];
       oa.n[c] = (int64_t)cs[c].trips.size();
       Trip* dt;
-      TRY(R.arena.get(&dt, std::max<size_t>(cs[c].trips.size(), 1)));
+      TRY(A.get(&dt, std::max<size_t>(cs[c].trips.size(), 1)));
       if (!cs[c].trips.empty())
         CU(cudaMemcpyAsync(dt, cs[c].trips.data(), cs[c].trips.size() * sizeof(Trip),
                            cudaMemcpyHostToDevice, R.st));
@@ -1301,6 +1216,256 @@ int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out,
   return LNO_OT_OK;
 }
 
+}  // namespace
+
+// Whole-domain operands kept between calls (options.keep_operands): the DF
+// blocks and scales of the Run and the operand tensors of both spin passes,
+// built for every triplet of the domain.  A later call on the same arrays
+// (another triplet selection) only runs the contractions and energy kernels.
+struct DomainCache {
+  lno_ot_domain key{};      // arrays and sizes the operands were built from
+  int prec = 0;
+  std::unique_ptr<Run> R;
+  CaseSel cs[4];            // full selections at build time, the call's afterwards
+  std::unique_ptr<SpinPass> pa, pb;
+  bool has_a = false, has_b = false;
+
+  bool matches(const lno_ot_domain* d, int p) const {
+    if (p != prec || d->nbas != key.nbas || d->naux != key.naux) return false;
+    for (int s = 0; s < 2; ++s)
+      if (d->nocc[s] != key.nocc[s] || d->B[s] != key.B[s] || d->eps[s] != key.eps[s] ||
+          d->t1[s] != key.t1[s] || d->fov[s] != key.fov[s])
+        return false;
+    return d->t2aa == key.t2aa && d->t2bb == key.t2bb && d->t2ab == key.t2ab;
+  }
+};
+
+void destroy_cache(DomainCache* c) {
+  if (!c) return;
+  c->pa.reset();  // spin-pass operands first, then the Run's DF blocks
+  c->pb.reset();
+  c->R.reset();
+  delete c;
+}
+
+namespace {
+
+// Settings of an internal energy pass over an augmented domain (the central
+// LMOs of the Laplace form): explicit triplet lists, per-spin orbital counts,
+// internal occupied ranges, one quadrature point and eq local_pt's partition.
+struct PassSpec {
+  const CaseSel* cs;   // [4]
+  int nbs[2];
+  int noi[2];
+  double lap_s, lap_w;
+};
+
+void set_precision(Run& R, int prec) {
+  R.f64 = prec == LNO_OT_FP64;
+  R.S = prec == LNO_OT_BF16X6    ? 3
+        : prec == LNO_OT_BF16X10 ? 4
+        : prec == LNO_OT_BF16X15 ? 5
+                                 : 2;
+  R.Sdf = prec == LNO_OT_BF16X15 ? 5 : 4;
+}
+
+// Integral scale of the sliced path: one pass over every DF block the two
+// spin passes need (their current selections).
+int measure_sigI(lno_ot_ctx* ctx, Run& R, SpinPass* pa, SpinPass* pb) {
+  if (R.f64) return LNO_OT_OK;
+  if (pa) pa->plan();
+  if (pb) pb->plan();
+  if (pa) TRY(pa->prepare_inputs());
+  if (pb) TRY(pb->prepare_inputs());
+  CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), R.st));
+  if (pa) TRY(pa->measure());
+  if (pb) TRY(pb->measure());
+  unsigned long long h;
+  CU(cudaMemcpyAsync(&h, ctx->d_amax, sizeof h, cudaMemcpyDeviceToHost, R.st));
+  CU(cudaStreamSynchronize(R.st));
+  double m;
+  std::memcpy(&m, &h, 8);
+  R.sigI = pow2_scale(2.0 * m);  // antisymmetrised combinations are <= 2 max
+  return LNO_OT_OK;
+}
+
+// Builds ctx->cache for dom (every triplet of the domain).
+int build_cache(lno_ot_ctx* ctx, const lno_ot_domain* dom) {
+  destroy_cache(ctx->cache);
+  ctx->cache = nullptr;
+  std::unique_ptr<DomainCache> C(new DomainCache());
+  C->key = *dom;
+  for (int c = 0; c < 4; ++c) {
+    C->key.e_trip[c] = nullptr;
+    C->key.trip_sel[c] = nullptr;
+    C->key.n_sel[c] = 0;
+  }
+  C->key.e_orb[0] = C->key.e_orb[1] = nullptr;
+  C->prec = ctx->prec;
+  C->R.reset(new Run(ctx, &C->key));
+  Run& R = *C->R;
+  set_precision(R, ctx->prec);
+  for (int c = 0; c < 4; ++c) TRY(select_case(&C->key, c, C->cs[c]));
+  TRY(R.stage());
+  C->has_a = !C->cs[0].trips.empty() || !C->cs[1].trips.empty();
+  C->has_b = !C->cs[3].trips.empty() || !C->cs[2].trips.empty();
+  C->pa.reset(new SpinPass(R, 0, C->cs[0], C->cs[1], nullptr, nullptr));
+  C->pb.reset(new SpinPass(R, 1, C->cs[3], C->cs[2], nullptr, nullptr));
+  TRY(measure_sigI(ctx, R, C->has_a ? C->pa.get() : nullptr, C->has_b ? C->pb.get() : nullptr));
+  if (C->has_a) TRY(C->pa->prepare());
+  if (C->has_b) TRY(C->pb->prepare());
+  CU(cudaStreamSynchronize(R.st));
+  ctx->cache = C.release();
+  return LNO_OT_OK;
+}
+
+// One call through the cache (built on a miss).  Returns LNO_OT_ENOMEM when
+// the whole-domain operands do not fit; the caller then runs uncached.
+int cached_energy(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out) {
+  ctx->stats = lno_ot_stats{};
+  ctx->ev_used = 0;
+  CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+  cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr;
+  const bool hit = ctx->cache && ctx->cache->matches(dom, ctx->prec);
+  {
+    // events from the pool (the Run may not exist yet)
+    for (cudaEvent_t* e : {&t0, &t1, &t2}) {
+      if (ctx->ev_used == ctx->ev_pool.size()) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+          cudaGetLastError();
+          break;
+        }
+        ctx->ev_pool.push_back(ev);
+      }
+      *e = ctx->ev_pool[ctx->ev_used++];
+    }
+  }
+  if (t0) cudaEventRecord(t0, ctx->stream);
+  if (!hit) {
+    const int rc = build_cache(ctx, dom);
+    if (rc != LNO_OT_OK) {
+      destroy_cache(ctx->cache);
+      ctx->cache = nullptr;
+      cudaGetLastError();
+      return rc;
+    }
+  }
+  DomainCache* C = ctx->cache;
+  Run& R = *C->R;
+  R.dom = dom;
+  R.contract_ev.clear();
+  R.energy_ev.clear();
+  if (t1) cudaEventRecord(t1, R.st);
+  CaseSel sel[4];
+  for (int c = 0; c < 4; ++c) {
+    TRY(select_case(dom, c, sel[c]));
+    C->cs[c].trips.swap(sel[c].trips);
+    C->cs[c].ntot = sel[c].ntot;
+  }
+  Arena A(R.st, ctx->ws_limit);
+  double* e_int[4];
+  for (int c = 0; c < 4; ++c)
+    TRY(A.get(&e_int[c], std::max<size_t>(C->cs[c].trips.size(), 1)));
+  C->pa->e_same = e_int[0];
+  C->pa->e_mixed = e_int[1];
+  C->pb->e_same = e_int[3];
+  C->pb->e_mixed = e_int[2];
+  if (C->has_a) TRY(C->pa->compute());
+  if (C->has_b) TRY(C->pb->compute());
+  return finish_call(ctx, R, A, dom, C->cs, e_int, false, t0, t1, t2, out);
+}
+
+bool flip_candidate(const lno_ot_domain* dom) {
+  bool flip = dom->nocc[0] == dom->nocc[1] && dom->B[0] == dom->B[1] &&
+              dom->eps[0] == dom->eps[1] && dom->t1[0] == dom->t1[1] &&
+              dom->t2aa == dom->t2bb && dom->fov[0] == dom->fov[1];
+  for (int c = 0; c < 4; ++c) flip = flip && dom->trip_sel[c] == nullptr;
+  return flip;
+}
+
+int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out,
+                const PassSpec* spec = nullptr) {
+  if (!spec) TRY(validate(ctx, dom));
+  if (ctx->prec == LNO_OT_TF32) return LNO_OT_EUNSUPPORTED;
+  CU(cudaSetDevice(ctx->device));
+  if (!spec && ctx->keep && !flip_candidate(dom)) {
+    const int rc = cached_energy(ctx, dom, out);
+    if (rc != LNO_OT_ENOMEM) return rc;   // the whole domain did not fit: run uncached
+  }
+  if (!spec) ctx->stats = lno_ot_stats{};
+  ctx->ev_used = 0;
+  Run R(ctx, dom);
+  if (spec) {
+    for (int s = 0; s < 2; ++s) {
+      R.nbs[s] = spec->nbs[s];
+      R.noi[s] = spec->noi[s];
+    }
+    R.lap_s = spec->lap_s;
+    R.lap_w = spec->lap_w;
+  }
+  set_precision(R, ctx->prec);
+  CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+  cudaEvent_t t0 = R.event(), t1 = R.event(), t2 = R.event();
+  if (t0) cudaEventRecord(t0, R.st);
+
+  CaseSel cs[4];
+  for (int c = 0; c < 4; ++c) {
+    if (spec)
+      cs[c] = spec->cs[c];
+    else
+      TRY(select_case(dom, c, cs[c]));
+  }
+  double* e_int[4];
+  for (int c = 0; c < 4; ++c)
+    TRY(R.arena.get(&e_int[c], std::max<size_t>(cs[c].trips.size(), 1)));
+  // Closed-shell domain (both spins given by the same arrays, spin-flip
+  // symmetric mixed amplitudes): bbb and abb are the spin-flip images of aaa
+  // and aab, with identical values, so only the spin-up pass runs.
+  bool flip = flip_candidate(dom) && spec == nullptr;
+  if (flip && dom->nocc[0] > 0 && dom->nocc[0] < dom->nbas) {
+    // symmetric to within 1e-12 of the largest amplitude: amplitudes from a
+    // closed-shell calculation agree with their spin-flip images to rounding
+    const int n = dom->nocc[0], v = dom->nbas - dom->nocc[0];
+    CU(cudaMemsetAsync(ctx->d_amax, 0, sizeof(unsigned long long), R.st));
+    CU(launch_absmax(dom->t2ab, (int64_t)n * n * v * v, ctx->d_amax, R.st));
+    unsigned long long hm = 0;
+    CU(cudaMemcpyAsync(&hm, ctx->d_amax, sizeof hm, cudaMemcpyDeviceToHost, R.st));
+    CU(cudaStreamSynchronize(R.st));
+    double amax;
+    std::memcpy(&amax, &hm, 8);
+    unsigned int* cnt;
+    TRY(R.arena.get(&cnt, 1));
+    CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), R.st));
+    CU(launch_t2ab_flip_mismatch(dom->t2ab, n, v, 1e-12 * amax, cnt, R.st));
+    unsigned int h = 1;
+    CU(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, R.st));
+    CU(cudaStreamSynchronize(R.st));
+    R.stats->other_launches += 2;
+    flip = h == 0;
+  }
+  TRY(R.stage());
+  {
+    SpinPass pa(R, 0, cs[0], cs[1], e_int[0], e_int[1]);
+    SpinPass pb(R, 1, cs[3], cs[2], e_int[3], e_int[2]);
+    // integral scale: first pass over every DF block both spins need
+    TRY(measure_sigI(ctx, R, &pa, flip ? nullptr : &pb));
+    if (t1) cudaEventRecord(t1, R.st);
+    TRY(pa.run());
+    pa.own.release();
+    if (!flip) {
+      TRY(pb.run());
+    } else {  // spin-flip images: bbb = aaa, abb = aab, triplet for triplet
+      if (!cs[3].trips.empty())
+        CU(cudaMemcpyAsync(e_int[3], e_int[0], cs[3].trips.size() * sizeof(double),
+                           cudaMemcpyDeviceToDevice, R.st));
+      if (!cs[2].trips.empty())
+        CU(cudaMemcpyAsync(e_int[2], e_int[1], cs[2].trips.size() * sizeof(double),
+                           cudaMemcpyDeviceToDevice, R.st));
+    }
+  }
+  return finish_call(ctx, R, R.arena, dom, cs, e_int, spec != nullptr, t0, t1, t2, out);
+}
 
 // ---------------------------------------------------------------------------
 // Natural auxiliary functions (Sec. 3.6, eq naf_w), float64 (naf.cu).
@@ -1389,7 +1554,7 @@ int naf_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double eps, double* cons
 int central_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, const lno_ot_central* c) {
   if (!c) return LNO_OT_EINVAL;
   TRY(validate(ctx, dom));
-  if (c->nq < 1 || c->nq > 32 || !c->s || !c->w || c->spin < 0 || c->spin > 1 || c->nlmo < 0)
+  if (c->nq < 1 || c->nq > 256 || !c->s || !c->w || c->spin < 0 || c->spin > 1 || c->nlmo < 0)
     return LNO_OT_EINVAL;
   if (c->nlmo > 0 && !c->dE) return LNO_OT_EINVAL;
   for (int q = 0; q < c->nq; ++q)
@@ -1969,6 +2134,7 @@ int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
     std::sort(c->tune.begin(), c->tune.end(),
               [](const lno_ot_ctx::TuneRow& a, const lno_ot_ctx::TuneRow& b) { return a.vmax < b.vmax; });
   }
+  c->keep = opt->keep_operands != 0;
   // NULL = the legacy default stream (ordered with every blocking stream)
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->own_stream = false;
@@ -1991,6 +2157,9 @@ int lno_ot_init(lno_ot_ctx** ctx, const lno_ot_options* opt) {
 void lno_ot_destroy(lno_ot_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  destroy_cache(c->cache);
+  c->cache = nullptr;
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   cudaFree(c->d_flag);
@@ -2055,6 +2224,18 @@ int lno_ot_naf(lno_ot_ctx* ctx, const lno_ot_domain* dom, double eps_naf, double
 int lno_ot_laplace_quadrature(double xmin, double xmax, double tol, int nmax, double* s,
                               double* w, int* nq) {
   return laplace_quadrature(xmin, xmax, tol, nmax, s, w, nq);
+}
+
+int lno_ot_release(lno_ot_ctx* ctx) {
+  if (!ctx) return LNO_OT_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return LNO_OT_ECUDA;
+  }
+  destroy_cache(ctx->cache);
+  ctx->cache = nullptr;
+  CU(cudaStreamSynchronize(ctx->stream));
+  return LNO_OT_OK;
 }
 
 int lno_ot_last_stats(const lno_ot_ctx* ctx, lno_ot_stats* st) {

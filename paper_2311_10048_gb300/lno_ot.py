@@ -24,7 +24,8 @@ CASES = ("aaa", "aab", "abb", "bbb")
 
 class Options(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p),
-                ("workspace_bytes", C.c_size_t), ("tune_cache", C.c_char_p)]
+                ("workspace_bytes", C.c_size_t), ("tune_cache", C.c_char_p),
+                ("keep_operands", C.c_int)]
 
 
 class Domain(C.Structure):
@@ -104,6 +105,8 @@ def load_library(build_if_missing=False):
     lib.lno_ot_last_error.restype = C.c_char_p
     lib.lno_ot_energy_central.argtypes = [C.c_void_p, C.POINTER(Domain), C.POINTER(Central)]
     lib.lno_ot_energy_central.restype = C.c_int
+    lib.lno_ot_release.argtypes = [C.c_void_p]
+    lib.lno_ot_release.restype = C.c_int
     lib.lno_ot_naf.argtypes = [C.c_void_p, C.POINTER(Domain), C.c_double, C.c_void_p * 2,
                                C.POINTER(C.c_int), C.c_void_p]
     lib.lno_ot_naf.restype = C.c_int
@@ -188,7 +191,7 @@ class Context:
     """An lno_ot context (device, precision, stream)."""
 
     def __init__(self, device=0, precision="fp64", stream=None, workspace_bytes=0,
-                 tune_cache=None):
+                 tune_cache=None, keep_operands=False):
         self.lib = load_library()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if stream is None:  # order the library's work after torch's pending work
@@ -197,7 +200,7 @@ class Context:
                 stream = torch.cuda.current_stream(device).cuda_stream or None
         self._tune = None if tune_cache is None else str(tune_cache).encode()
         opt = Options(device, prec, None if stream is None else C.c_void_p(stream), workspace_bytes,
-                      self._tune)
+                      self._tune, 1 if keep_operands else 0)
         h = C.c_void_p()
         rc = self.lib.lno_ot_init(C.byref(h), C.byref(opt))
         if rc != OK:
@@ -227,6 +230,12 @@ class Context:
         out = dict(zip(CASES + ("total",), list(r.e)))
         out["status"] = rc
         return out
+
+    def release(self):
+        """Free the operands kept by keep_operands (lno_ot_release)."""
+        rc = self.lib.lno_ot_release(self.h)
+        if rc != OK:
+            raise LnoError(rc, "lno_ot_release")
 
     def energy_raw(self, d):
         """Call lno_ot_energy on a prepared Domain struct; returns (rc, Result)."""

@@ -298,3 +298,36 @@ def test_c4_bf16x15_per_triplet(ctx15):
     # sqrt(8436) over the domain
     assert abs(out["total"] - g["total"]) <= 3e-8
     print("c4 bf16x15 worst per-triplet |dE| =", worst)
+
+
+def test_kept_operands_give_the_whole_domain_per_triplet_values(lib):
+    # blocks of triplets through a context that keeps the operands equal, bit
+    # for bit, one uncached call over the whole domain; release and a new
+    # domain rebuild them
+    d = make_domain(60, (7, 5), naux=100, L=25.0, seed=12, t1_sd=0.02)
+    dd = lno_ot.to_device(d)
+    na, nb = dd["nocc"]
+    n = [T.n_triplets(c, na, nb) for c in CASES]
+    for prec in ("bf16x10", "fp64"):
+        ref_ctx = lno_ot.Context(0, prec)
+        ref = [torch.zeros(k, dtype=torch.float64, device="cuda") for k in n]
+        tot = ref_ctx.energy(dd, e_trip=ref)["total"]
+        ref_ctx.close()
+        ctx = lno_ot.Context(0, prec, keep_operands=True)
+        for rep in range(2):
+            got = [torch.full((k,), float("nan"), dtype=torch.float64, device="cuda") for k in n]
+            K = 3
+            for s in range(K):
+                sel = [np.arange(k * s // K, k * (s + 1) // K, dtype=np.int64) for k in n]
+                views = [got[ci][sel[ci][0]:sel[ci][-1] + 1] if len(sel[ci]) else None
+                         for ci in range(4)]
+                ctx.energy(dd, e_trip=views, trip_sel=sel)
+            for ci in range(4):
+                assert torch.equal(got[ci], ref[ci]), (prec, rep, CASES[ci])
+            assert ctx.energy(dd)["total"] == tot
+            ctx.release()
+        other = lno_ot.to_device(config_domain("c0"))
+        e0 = ctx.energy(other)["total"]
+        ctx.close()
+        g = golden("c0")
+        assert abs(e0 - g["total"]) <= 1e-8
