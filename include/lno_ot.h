@@ -71,7 +71,14 @@ typedef enum {
  *          about 1.5x its contraction time.  The reference mode against which
  *          the domain-total error of the faster modes is measured when a
  *          float64 run of a whole domain is too slow.
- *  TF32    reserved; returns LNO_OT_EUNSUPPORTED in this build. */
+ *  TF32    tensor cores on their TF32 path (kind::tf32): every float64
+ *          operand split into 2 TF32 slices of 11 significant bits with an
+ *          exact power-of-two scale, 3 slice products per multiply, one FP32
+ *          accumulator per weight class.  Unlike the BF16 modes the class
+ *          sums are not exact (11-bit x 11-bit products overflow the FP32
+ *          significand after a few terms), so the accumulation rounds; it is
+ *          about as fast as BF16X6 (TF32 runs at half the BF16 rate) and less
+ *          accurate: provided for comparison, with its error measured. */
 typedef enum {
   LNO_OT_FP64 = 0,
   LNO_OT_BF16X3 = 1,

@@ -139,14 +139,14 @@ struct TcDiag {
 
 // tc_gemm.cu: grouped sliced contraction.  mA: maps with 128-row boxes,
 // mB: maps with BN-row boxes; instances (S, BN, OutT) are listed there.
-template <int S, int BN, typename OutT>
+template <int S, int BN, typename OutT, bool TF = false>
 cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
                            int nprob, int M, int N, int ldo, double scale, int* flag,
                            unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag);
 long long tc_default_wait_cycles();
 inline TcDiag tc_normal() { return TcDiag{tc_default_wait_cycles(), 0}; }
 int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
-                     int64_t slice_stride, int box_rows);
+                     int64_t slice_stride, int box_rows, int esz = 2);
 int sliced_product_bn(int S);
 cudaError_t launch_sliced_product(int S, const CUtensorMap* mA, const CUtensorMap* mB,
                                   const TcProb* dp, int M, int N, double scale, int* flag,
@@ -196,6 +196,28 @@ struct StoreSlices {
       x -= q;                        // exact
       p[s * slice_stride + idx] = __double2bfloat16(q);
       w *= 256.0;
+    }
+  }
+};
+
+// Exact TF32 slices (stored as float): value = scale 2^-10 (s_0 + ... +
+// s_{S-1}), s_0 an integer in [-1024, 1024], s_q a multiple of 2^(-11q): 11
+// significant bits each, what one TF32 operand holds.
+template <int S>
+struct StoreTF32 {
+  float* p;
+  int64_t slice_stride;
+  double inv_t;          // 2^10 / amplitude scale
+  double inv_i;          // 2^10 / integral scale
+  __device__ __forceinline__ void operator()(int64_t idx, double v, int part) const {
+    double x = v * (part ? inv_i : inv_t);
+    double w = 1.0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      double q = rint(x * w) / w;   // w = 2^(11s): exact scaling
+      x -= q;
+      p[s * slice_stride + idx] = (float)q;
+      w *= 2048.0;
     }
   }
 };

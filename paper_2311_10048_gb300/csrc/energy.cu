@@ -353,13 +353,34 @@ __device__ __forceinline__ float div_nr(float num, float D) {
   return __fmul_rn(num, r);
 }
 
+// exp(x) in float for x <= 0: Cody-Waite reduction x = k ln2 + r, |r| <= ln2/2
+// (ln2 split into a 16-bit head and its tail), a degree-7 Taylor polynomial of
+// exp(r) by Horner (truncation < 6e-9 relative), and 2^k by the exponent
+// field.  Every step rounds to nearest, so the result carries no systematic
+// bias (a library exp with an average bias of a fraction of an ulp would
+// shift every Laplace factor, and the energy, by that fraction).
+__device__ __forceinline__ float exp_neg(float x) {
+  if (x < -87.0f) return 0.0f;
+  const float k = rintf(__fmul_rn(x, 1.44269504088896341f));      // x / ln2
+  const float r = __fmaf_rn(-k, 1.42860682030941723e-6f, __fmaf_rn(-k, 0.693145751953125f, x));
+  float p = 1.0f / 5040.0f;
+  p = __fmaf_rn(p, r, 1.0f / 720.0f);
+  p = __fmaf_rn(p, r, 1.0f / 120.0f);
+  p = __fmaf_rn(p, r, 1.0f / 24.0f);
+  p = __fmaf_rn(p, r, 1.0f / 6.0f);
+  p = __fmaf_rn(p, r, 0.5f);
+  p = __fmaf_rn(p, r, 1.0f);
+  p = __fmaf_rn(p, r, 1.0f);
+  return __fmul_rn(p, __int_as_float(((int)k + 127) << 23));
+}
+
 // Laplace factor exp(s D) of one element (D < 0, so the argument is <= 0),
 // with s carried as a float pair (s_hi + s_lo): rounding s to one float would
 // shift every factor by the same relative amount, a bias; the quadrature
 // weight -w is applied to the float64 partial sums instead, for the same
 // reason.
 __device__ __forceinline__ float lap_factor(float shi, float slo, float D) {
-  return expf(__fmaf_rn(shi, D, __fmul_rn(slo, D)));
+  return exp_neg(__fmaf_rn(shi, D, __fmul_rn(slo, D)));
 }
 
 // Energy of float32 X with register prefetch of the next cube tile.

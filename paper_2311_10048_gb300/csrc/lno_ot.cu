@@ -237,7 +237,9 @@ struct Operand {
   int64_t rows = 0;  // rows per slot
   int K = 0, Kp = 0;
   double* f64 = nullptr;
-  __nv_bfloat16* bf = nullptr;
+  __nv_bfloat16* bf = nullptr;   // BF16 slices
+  float* f32 = nullptr;          // TF32 slices (stored as float)
+  int esz = 2;                   // bytes per slice element
   int S = 0;
   int64_t slice_stride = 0;
   CUtensorMap map128, map256, map64;  // TMA maps with boxes of 128 (A role, B of BN 128), 256, 64 rows
@@ -260,7 +262,7 @@ const CUtensorMap& map_for(const Operand& op, int box) {
 }
 
 // One grouped W-contraction launch with float32 output.
-cudaError_t launch_contract(int S, int bn_req, const Operand& A0, const Operand& A1,
+cudaError_t launch_contract(int S, bool tf, int bn_req, const Operand& A0, const Operand& A1,
                             const Operand& B0, const Operand& B1, const TcProb* dpt, int nprob,
                             int M, int N, int ldo, double scale, int* flag, int nsm,
                             cudaStream_t st) {
@@ -270,6 +272,12 @@ cudaError_t launch_contract(int S, int bn_req, const Operand& A0, const Operand&
   const TcDiag dg = tc_normal();
 #define LNO_CALL(SS, BB) \
   launch_tc_gemm<SS, BB, float>(mA, mB, dpt, nprob, M, N, ldo, scale, flag, nullptr, nsm, st, dg)
+  if (tf)
+    return bn == 128
+               ? launch_tc_gemm<2, 128, float, true>(mA, mB, dpt, nprob, M, N, ldo, scale, flag,
+                                                     nullptr, nsm, st, dg)
+               : launch_tc_gemm<2, 256, float, true>(mA, mB, dpt, nprob, M, N, ldo, scale, flag,
+                                                     nullptr, nsm, st, dg);
   if (S == 2) return bn == 128 ? LNO_CALL(2, 128) : LNO_CALL(2, 256);
   if (S == 3) return bn == 64 ? LNO_CALL(3, 64) : LNO_CALL(3, 128);
   if (S == 4) return bn == 64 ? LNO_CALL(4, 64) : LNO_CALL(4, 128);
@@ -283,6 +291,7 @@ struct Run {
   cudaStream_t st;
   Arena arena;
   bool f64;
+  bool tf32 = false;  // W contraction operands as TF32 slices (precision TF32)
   int S = 0;          // slices of the W contraction operands
   int Sdf = 4;        // slices of the DF factors
   double sigT = 1, sigI = 1, sigB = 1;
@@ -319,7 +328,9 @@ struct Run {
   int alloc_operand(Operand& op, int nslot, int64_t rows, int K, int S_) {
     return alloc_operand(arena, op, nslot, rows, K, S_);
   }
-  int alloc_operand(Arena& ar, Operand& op, int nslot, int64_t rows, int K, int S_) {
+  // tf: TF32 slices (the W operands of precision TF32); DF blocks are BF16
+  int alloc_operand(Arena& ar, Operand& op, int nslot, int64_t rows, int K, int S_,
+                    bool tf = false) {
     op.nslot = nslot;
     op.rows = rows;
     op.K = K;
@@ -330,11 +341,20 @@ struct Run {
       TRY(ar.get(&op.f64, (size_t)n));
     } else {
       op.slice_stride = round_up(n, 8);
-      TRY(ar.get(&op.bf, (size_t)(op.slice_stride * op.S)));
+      void* base;
+      if (tf) {
+        op.esz = 4;
+        TRY(ar.get(&op.f32, (size_t)(op.slice_stride * op.S)));
+        base = op.f32;
+      } else {
+        op.esz = 2;
+        TRY(ar.get(&op.bf, (size_t)(op.slice_stride * op.S)));
+        base = op.bf;
+      }
       const int64_t rows_ = std::max<int64_t>(op.total_rows(), 1);
-      TRY(make_operand_map(&op.map128, op.bf, op.Kp, rows_, op.S, op.slice_stride, 128));
-      TRY(make_operand_map(&op.map256, op.bf, op.Kp, rows_, op.S, op.slice_stride, 256));
-      TRY(make_operand_map(&op.map64, op.bf, op.Kp, rows_, op.S, op.slice_stride, 64));
+      TRY(make_operand_map(&op.map128, base, op.Kp, rows_, op.S, op.slice_stride, 128, op.esz));
+      TRY(make_operand_map(&op.map256, base, op.Kp, rows_, op.S, op.slice_stride, 256, op.esz));
+      TRY(make_operand_map(&op.map64, base, op.Kp, rows_, op.S, op.slice_stride, 64, op.esz));
     }
     return LNO_OT_OK;
   }
@@ -343,6 +363,9 @@ struct Run {
   template <int SS>
   StoreSlices<SS> slices(const Operand& op) const {
     return StoreSlices<SS>{op.bf, op.slice_stride, 128.0 / sigT, 128.0 / sigI};
+  }
+  StoreTF32<2> tf32_slices(const Operand& op) const {
+    return StoreTF32<2>{op.f32, op.slice_stride, 1024.0 / sigT, 1024.0 / sigI};
   }
 
   // ---- DF integrals: out[n][m] = sum_Q L[m][Q] R[n][Q] (float64) ------------
@@ -787,14 +810,18 @@ struct SpinPass {
   }
 
   int build() {
-    TRY(R.alloc_operand(own, AT, (int)listAT.size(), v, v + oi, R.S));
-    TRY(R.alloc_operand(own, BT, (int)listBT.size(), npairs(v), v + oi, R.S));
-    TRY(R.alloc_operand(own, A1, (int)listA1.size(), v, vt + oti, R.S));
-    TRY(R.alloc_operand(own, BG, (int)listBG.size(), (int64_t)v * vt, vt + oti, R.S));
-    TRY(R.alloc_operand(own, BF, (int)listBF.size(), (int64_t)v * vt, v + oi, R.S));
-    TRY(R.alloc_operand(own, AT2, (int)listAT2.size(), vt, v + oi, R.S));
+    const bool tf = R.tf32;
+    TRY(R.alloc_operand(own, AT, (int)listAT.size(), v, v + oi, R.S, tf));
+    TRY(R.alloc_operand(own, BT, (int)listBT.size(), npairs(v), v + oi, R.S, tf));
+    TRY(R.alloc_operand(own, A1, (int)listA1.size(), v, vt + oti, R.S, tf));
+    TRY(R.alloc_operand(own, BG, (int)listBG.size(), (int64_t)v * vt, vt + oti, R.S, tf));
+    TRY(R.alloc_operand(own, BF, (int)listBF.size(), (int64_t)v * vt, v + oi, R.S, tf));
+    TRY(R.alloc_operand(own, AT2, (int)listAT2.size(), vt, v + oi, R.S, tf));
     if (R.f64) return pack_all(StoreF64{AT.f64}, StoreF64{BT.f64}, StoreF64{A1.f64},
                                StoreF64{BG.f64}, StoreF64{BF.f64}, StoreF64{AT2.f64});
+    if (tf)
+      return pack_all(R.tf32_slices(AT), R.tf32_slices(BT), R.tf32_slices(A1),
+                      R.tf32_slices(BG), R.tf32_slices(BF), R.tf32_slices(AT2));
     if (R.S == 2)
       return pack_all(R.slices<2>(AT), R.slices<2>(BT), R.slices<2>(A1), R.slices<2>(BG),
                       R.slices<2>(BF), R.slices<2>(AT2));
@@ -819,8 +846,8 @@ struct SpinPass {
       CU(launch_gemm_f64(dpf, nprob, M, N, ldo, R.st));
     } else {
       CU(cudaMemcpyAsync(dpt, pt.data(), nprob * sizeof(TcProb), cudaMemcpyHostToDevice, R.st));
-      const double scale = R.sigT * R.sigI * std::ldexp(1.0, -14);
-      CU(launch_contract(R.S, bn, opA0, opA1, opB0, opB1, dpt, nprob, M, N, ldo, scale,
+      const double scale = R.sigT * R.sigI * std::ldexp(1.0, R.tf32 ? -20 : -14);
+      CU(launch_contract(R.S, R.tf32, bn, opA0, opA1, opB0, opB1, dpt, nprob, M, N, ldo, scale,
                          R.ctx->d_flag, R.ctx->nsm, R.st));
     }
     if (e1) cudaEventRecord(e1, R.st);
@@ -1262,6 +1289,7 @@ struct PassSpec {
 
 void set_precision(Run& R, int prec) {
   R.f64 = prec == LNO_OT_FP64;
+  R.tf32 = prec == LNO_OT_TF32;
   R.S = prec == LNO_OT_BF16X6    ? 3
         : prec == LNO_OT_BF16X10 ? 4
         : prec == LNO_OT_BF16X15 ? 5
@@ -1387,7 +1415,6 @@ bool flip_candidate(const lno_ot_domain* dom) {
 int energy_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, lno_ot_result* out,
                 const PassSpec* spec = nullptr) {
   if (!spec) TRY(validate(ctx, dom));
-  if (ctx->prec == LNO_OT_TF32) return LNO_OT_EUNSUPPORTED;
   CU(cudaSetDevice(ctx->device));
   if (!spec && ctx->keep && !flip_candidate(dom)) {
     const int rc = cached_energy(ctx, dom, out);
@@ -1560,7 +1587,6 @@ int central_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, const lno_ot_central
   for (int q = 0; q < c->nq; ++q)
     if (!(c->s[q] > 0.0) || !std::isfinite(c->s[q]) || !std::isfinite(c->w[q]))
       return LNO_OT_EINVAL;
-  if (ctx->prec == LNO_OT_TF32) return LNO_OT_EUNSUPPORTED;
   const int sg = c->spin, tg = 1 - sg, P = c->nlmo;
   const int nbas = dom->nbas, naux = dom->naux;
   const int na = dom->nocc[0], nb = dom->nocc[1], o = dom->nocc[sg];

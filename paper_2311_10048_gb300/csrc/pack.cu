@@ -425,6 +425,7 @@ LNO_INST(StoreSlices<2>)
 LNO_INST(StoreSlices<3>)
 LNO_INST(StoreSlices<4>)
 LNO_INST(StoreSlices<5>)
+LNO_INST(StoreTF32<2>)
 #undef LNO_INST
 
 }  // namespace lno

@@ -47,7 +47,7 @@ namespace lno {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 32;                     // 64-byte rows, SWIZZLE_64B
+constexpr int BK = 32;                     // BF16 elements per 64-byte row, SWIZZLE_64B
 constexpr long long kWaitCycles = 4000000000LL;
 constexpr int kSmemBudget = 227 * 1024;
 
@@ -123,6 +123,16 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       : "memory");
 }
 
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -164,11 +174,13 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: kind::f16, A/B BF16 K-major, D FP32, M=128, N=BN.
-template <int BN>
-__device__ __forceinline__ uint32_t idesc_bf16(int neg) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)neg << 13) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: D FP32, A/B K-major of format 1 (BF16, kind::f16)
+// or 2 (TF32, kind::tf32), M=128, N=BN.
+template <int BN, bool TF>
+__device__ __forceinline__ uint32_t idesc_mma(int neg) {
+  constexpr uint32_t fmt = TF ? 2u : 1u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)neg << 13) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 template <int S, int BN>
@@ -188,13 +200,18 @@ struct Cfg {
 // at all, so the MMA thread's first wait (on a full barrier nothing will
 // complete) runs out after wait_cycles and the kernel takes its error exit
 // with nothing in flight.  Library calls always pass {kWaitCycles, 0}.
-template <int S, int BN, typename OutT>
+// TF: TF32 slices (32-bit elements, 16 per 64-byte row, K 8 per MMA) instead
+// of BF16 ones (32 per row, K 16 per MMA); the shared-memory layout, the
+// descriptors and the MMAs per row are the same in bytes.
+template <int S, int BN, typename OutT, bool TF>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
                const TcProb* __restrict__ probs, int nprob, int M, int N, int ldo, double scale,
                int* __restrict__ flag, unsigned long long* __restrict__ amax, TcDiag diag) {
   using C = Cfg<S, BN>;
+  constexpr int BKE = TF ? BK / 2 : BK;   // elements per 64-byte row
+  constexpr int KM = TF ? 8 : 16;         // K of one MMA
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -261,7 +278,7 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
           const TcSeg seg = P.seg[sg];
           const CUtensorMap* ma = seg.amap ? &mapA1 : &mapA0;
           const CUtensorMap* mb = seg.bmap ? &mapB1 : &mapB0;
-          for (int k0 = 0; k0 < seg.K; k0 += BK) {
+          for (int k0 = 0; k0 < seg.K; k0 += BKE) {
             if (!mbar_wait(empty_bar(stage), phase ^ 1u, flag, 1, true, wlim)) {
               ok = false;
               break;
@@ -305,16 +322,16 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
         uint32_t cls_on = 0;  // bit g: accumulator of class g already written
         for (int sg = 0; sg < P.nseg && ok; ++sg) {
           const TcSeg seg = P.seg[sg];
-          const uint32_t idesc = idesc_bf16<BN>(seg.neg);
-          for (int k0 = 0; k0 < seg.K; k0 += BK) {
+          const uint32_t idesc = idesc_mma<BN, TF>(seg.neg);
+          for (int k0 = 0; k0 < seg.K; k0 += BKE) {
             if (!mbar_wait(full_bar(stage), phase, flag, 3, true, wlim)) {
               ok = false;
               break;
             }
             tc_fence_after();
 #pragma unroll
-            for (int ks = 0; ks < BK / 16; ++ks) {
-              if (k0 + ks * 16 < seg.K) {
+            for (int ks = 0; ks < 2; ++ks) {   // two 32-byte MMA steps per 64-byte row
+              if (k0 + ks * KM < seg.K) {
 #pragma unroll
                 for (int pa = 0; pa < S; ++pa) {
 #pragma unroll
@@ -322,7 +339,10 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                     const uint64_t ad = sdesc_sw64(a_addr(stage, pa) + ks * 32);
                     const uint64_t bd = sdesc_sw64(b_addr(stage, pb) + ks * 32);
                     const int g = pa + pb;
-                    umma_bf16(tmem + g * BN, ad, bd, idesc, (cls_on >> g) & 1u);
+                    if constexpr (TF)
+                      umma_tf32(tmem + g * BN, ad, bd, idesc, (cls_on >> g) & 1u);
+                    else
+                      umma_bf16(tmem + g * BN, ad, bd, idesc, (cls_on >> g) & 1u);
                     cls_on |= 1u << g;
                     any = true;
                   }
@@ -470,31 +490,35 @@ static EncodeTiledFn get_encode() {
   return fn;
 }
 
-// 3-D map over a sliced operand tensor: (k < Kp, row < rows, slice < S).
-// Box: 32 k x box_rows rows x 1 slice, 64-byte swizzle, zero fill.
+// 3-D map over a sliced operand tensor: (k < Kp, row < rows, slice < S) of
+// esz-byte elements (2: BF16, 4: TF32 values stored as float).
+// Box: one 64-byte row of k x box_rows rows x 1 slice, 64-byte swizzle, zero fill.
 int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
-                     int64_t slice_stride, int box_rows) {
+                     int64_t slice_stride, int box_rows, int esz) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return LNO_OT_ECUDA;
-  if (Kp % 8 || slice_stride % 8 || (reinterpret_cast<uintptr_t>(base) & 15)) return LNO_OT_EINVAL;
+  if ((esz != 2 && esz != 4) || Kp % 8 || slice_stride % 8 ||
+      (reinterpret_cast<uintptr_t>(base) & 15))
+    return LNO_OT_EINVAL;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)S};
-  cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(slice_stride * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kp * esz), (cuuint64_t)(slice_stride * esz)};
+  cuuint32_t box[3] = {(cuuint32_t)(64 / esz), (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
-                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+  CUresult r = enc(map, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   3, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? LNO_OT_OK : LNO_OT_ECUDA;
 }
 
 // mB must be maps with boxes of BN rows; mA boxes of 128 rows.
-template <int S, int BN, typename OutT>
+template <int S, int BN, typename OutT, bool TF>
 cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
                            int nprob, int M, int N, int ldo, double scale, int* flag,
                            unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag) {
   using C = Cfg<S, BN>;
   if (nprob <= 0 || M <= 0 || N <= 0) return cudaSuccess;
-  auto k = tc_gemm_sliced<S, BN, OutT>;
+  auto k = tc_gemm_sliced<S, BN, OutT, TF>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   if (e != cudaSuccess) return e;
   const long long ntiles = (long long)nprob * ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
@@ -525,10 +549,11 @@ cudaError_t launch_sliced_product(int S, const CUtensorMap* mA, const CUtensorMa
 }
 long long tc_default_wait_cycles() { return kWaitCycles; }
 
-#define LNO_TC_INST(S, BN, T)                                                                    \
-  template cudaError_t launch_tc_gemm<S, BN, T>(const CUtensorMap*, const CUtensorMap*,          \
-                                                const TcProb*, int, int, int, int, double, int*, \
-                                                unsigned long long*, int, cudaStream_t, TcDiag);
+#define LNO_TC_INST(S, BN, T)                                                                   \
+  template cudaError_t launch_tc_gemm<S, BN, T, false>(const CUtensorMap*, const CUtensorMap*,  \
+                                                       const TcProb*, int, int, int, int, double, \
+                                                       int*, unsigned long long*, int,          \
+                                                       cudaStream_t, TcDiag);
 // W contractions (float32 output): slices x tile width
 LNO_TC_INST(2, 256, float)
 LNO_TC_INST(2, 128, float)
@@ -545,5 +570,14 @@ LNO_TC_INST(3, 128, double)
 LNO_TC_INST(4, 128, double)
 LNO_TC_INST(5, 64, double)
 #undef LNO_TC_INST
+// TF32 W contractions (2 TF32 slices, 3 products)
+template cudaError_t launch_tc_gemm<2, 256, float, true>(const CUtensorMap*, const CUtensorMap*,
+                                                         const TcProb*, int, int, int, int, double,
+                                                         int*, unsigned long long*, int,
+                                                         cudaStream_t, TcDiag);
+template cudaError_t launch_tc_gemm<2, 128, float, true>(const CUtensorMap*, const CUtensorMap*,
+                                                         const TcProb*, int, int, int, int, double,
+                                                         int*, unsigned long long*, int,
+                                                         cudaStream_t, TcDiag);
 
 }  // namespace lno

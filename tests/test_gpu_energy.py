@@ -331,3 +331,17 @@ def test_kept_operands_give_the_whole_domain_per_triplet_values(lib):
         ctx.close()
         g = golden("c0")
         assert abs(e0 - g["total"]) <= 1e-8
+
+
+def test_tf32_path_against_oracle(lib):
+    # TF32 slices with rounding FP32 accumulation: measured, not exact
+    g0, g4 = golden("c0"), golden("c4")
+    ctx = lno_ot.Context(0, "tf32")
+    out0, et0 = run_with_trip(ctx, config_domain("c0"))
+    out4 = ctx.energy(lno_ot.to_device(config_domain("c4")))
+    ctx.close()
+    err0 = max(abs(out0[c] - g0["cases"][c]["sum"]) for c in CASES)
+    err4 = abs(out4["total"] - g4["total"])
+    print("tf32: c0 worst case |dE| =", err0, " c4 total |dE| =", err4)
+    assert err0 <= 1e-6
+    assert err4 <= 1e-5 * abs(g4["total"])
