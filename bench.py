@@ -66,7 +66,11 @@ def peaks():
 # kernel last changed, and the line then reports traffic null).  The
 # per-launch traffic scales with the launch's tensor flops at a fixed virtual
 # space.
-DRAM_BYTES_PER_TENSOR_FLOP = {}
+DRAM_BYTES_PER_TENSOR_FLOP = {
+    # tc_gemm_sliced<4,128,float>, nbas 368 nocc 8/6 naux 1200 group: 10.646 GB
+    # over 15 331 800 MMAs of 128x128x16 (profiles/tc_gemm_sliced_bf16x10_c1shape.md)
+    "bf16x10": 10.646e9 / (15331800 * 128 * 128 * 16 * 2),
+}
 
 # FP32 operations per restricted (abc) element in the float32 energy kernel
 # (an FMA counts 2): W 2, V 17 (same spin) / 9 (mixed), W (W + V) 2,
