@@ -714,13 +714,16 @@ def run_domain(args):
             bias_u += (ntr[ci] * sd / math.sqrt(nn)) ** 2
             rnd += ntr[ci] * sd * sd
         bias_u, rnd = math.sqrt(bias_u), math.sqrt(rnd)
+        sig = math.sqrt(bias_u ** 2 + rnd ** 2)
+        verdict = ("yes" if abs(bias) + 3 * sig <= 1e-7
+                   else "no" if abs(bias) - 3 * sig > 1e-7 else "undetermined at 3 sigma")
         accuracy_fp64 = {
             "method": "per-triplet timed-precision minus float64-path values on the seeded "
                       "sample, per spin case; domain total = sum_c N_c x (mean_c, and the "
                       "rounding spread sqrt(N_c) sd_c)",
             "per_case": per_case, "bias_estimate_Eh": bias, "bias_estimate_1sigma_Eh": bias_u,
-            "rounding_1sigma_Eh": rnd,
-            "resolves_1e-7_Eh": bias_u < 1e-7 / 3}
+            "rounding_1sigma_Eh": rnd, "domain_total_estimate_Eh": [bias, sig],
+            "meets_1e-7_Eh": verdict}
 
     # domain-total error: the whole domain again in BF16X15
     accuracy = None if fp64 is None else {"vs_fp64_sample": accuracy_fp64}

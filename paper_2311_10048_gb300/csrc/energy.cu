@@ -439,45 +439,57 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   const float lslo = (float)(a.lap_s - (double)lshi);
 
   float4 xr[3][4];
+  uint32_t okm = 0;
   float vr[9];
   float t1r[3];
   float vrf[FU ? 5 : 1];
   float f1r[2];
   TwoF er;
-  bool ok1 = false, ok2 = false, ok3 = false;
 
+  // Fetch of a tile's three X sub-cubes, coalesced: in round u thread t loads
+  // the 16-byte chunk (t & 3) of sub-cube row R = 64 u + (t >> 2), so four
+  // neighbouring lanes read one 64-byte row and a warp reads 8 whole rows per
+  // load instruction.  okm bit (3 u + cube) marks the valid rows.
   auto fetch = [&](int q) {
     const int3 blk = a.blocks[q];
     const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
-    const float4* p1 = nullptr;
-    const float4* p2 = nullptr;
-    const float4* p3 = nullptr;
-    if (!MIXED) {
-      int b = b0 + r1, c = c0 + r2;
-      ok1 = b < c && c < nvs;
-      if (ok1) p1 = reinterpret_cast<const float4*>(Xg + pair_index(b, c) * a.pitch_x + a0);
-      int aa = a0 + r1;
-      ok2 = aa < c && c < nvs;
-      if (ok2) p2 = reinterpret_cast<const float4*>(Xg + pair_index(aa, c) * a.pitch_x + b0);
-      b = b0 + r2;
-      ok3 = aa < b && b < nvs;
-      if (ok3) p3 = reinterpret_cast<const float4*>(Xg + pair_index(aa, b) * a.pitch_x + c0);
-    } else {
-      int b = b0 + r1, c = c0 + r2;
-      ok1 = b < nvs && c < nvt;
-      if (ok1) p1 = reinterpret_cast<const float4*>(Xg + ((int64_t)b * nvt + c) * a.pitch_x + a0);
-      int aa = a0 + r1;
-      ok2 = aa < nvs && c < nvt;
-      if (ok2) p2 = reinterpret_cast<const float4*>(Xg + ((int64_t)aa * nvt + c) * a.pitch_x + b0);
-      b = b0 + r2;
-      ok3 = aa < b && b < nvs;
-      if (ok3) p3 = reinterpret_cast<const float4*>(Zg + pair_index(aa, b) * a.pitch_z + c0);
-    }
+    const int ch = (tid & 3) * 4;
+    okm = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (ok1) xr[0][u] = __ldg(p1 + u);
-      if (ok2) xr[1][u] = __ldg(p2 + u);
-      if (ok3) xr[2][u] = __ldg(p3 + u);
+      const int R = 64 * u + (tid >> 2);
+      const int s1 = R >> 4, s2 = R & 15;
+      const float4* p1 = nullptr;
+      const float4* p2 = nullptr;
+      const float4* p3 = nullptr;
+      bool k1, k2, k3;
+      if (!MIXED) {
+        int b = b0 + s1, c = c0 + s2;
+        k1 = b < c && c < nvs;
+        if (k1) p1 = reinterpret_cast<const float4*>(Xg + pair_index(b, c) * a.pitch_x + a0 + ch);
+        int aa = a0 + s1;
+        k2 = aa < c && c < nvs;
+        if (k2) p2 = reinterpret_cast<const float4*>(Xg + pair_index(aa, c) * a.pitch_x + b0 + ch);
+        b = b0 + s2;
+        k3 = aa < b && b < nvs;
+        if (k3) p3 = reinterpret_cast<const float4*>(Xg + pair_index(aa, b) * a.pitch_x + c0 + ch);
+      } else {
+        int b = b0 + s1, c = c0 + s2;
+        k1 = b < nvs && c < nvt;
+        if (k1)
+          p1 = reinterpret_cast<const float4*>(Xg + ((int64_t)b * nvt + c) * a.pitch_x + a0 + ch);
+        int aa = a0 + s1;
+        k2 = aa < nvs && c < nvt;
+        if (k2)
+          p2 = reinterpret_cast<const float4*>(Xg + ((int64_t)aa * nvt + c) * a.pitch_x + b0 + ch);
+        b = b0 + s2;
+        k3 = aa < b && b < nvs;
+        if (k3) p3 = reinterpret_cast<const float4*>(Zg + pair_index(aa, b) * a.pitch_z + c0 + ch);
+      }
+      if (k1) xr[0][u] = __ldg(p1);
+      if (k2) xr[1][u] = __ldg(p2);
+      if (k3) xr[2][u] = __ldg(p3);
+      okm |= (k1 ? 1u : 0u) << (3 * u) | (k2 ? 2u : 0u) << (3 * u) | (k3 ? 4u : 0u) << (3 * u);
     }
     if (!MIXED) {
       const int rows[3] = {b0, a0, a0}, cols[3] = {c0, c0, b0};
@@ -553,17 +565,17 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
     const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
     // ---- registers -> shared ----
     {
-      float4* d1 = reinterpret_cast<float4*>(T1 + (r1 * TB + r2) * P1);
-      float2* d2 = reinterpret_cast<float2*>(T2 + (r1 * TB + r2) * P2);
-      float4* d3 = reinterpret_cast<float4*>(T3 + (r1 * TB + r2) * P3);
+      const int ch = (tid & 3) * 4;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (ok1) d1[u] = xr[0][u];
-        if (ok2) {
-          d2[2 * u] = make_float2(xr[1][u].x, xr[1][u].y);
-          d2[2 * u + 1] = make_float2(xr[1][u].z, xr[1][u].w);
+        const int R = 64 * u + (tid >> 2);
+        if (okm & (1u << (3 * u))) *reinterpret_cast<float4*>(T1 + R * P1 + ch) = xr[0][u];
+        if (okm & (2u << (3 * u))) {
+          float2* d2 = reinterpret_cast<float2*>(T2 + R * P2 + ch);
+          d2[0] = make_float2(xr[1][u].x, xr[1][u].y);
+          d2[1] = make_float2(xr[1][u].z, xr[1][u].w);
         }
-        if (ok3) d3[u] = xr[2][u];
+        if (okm & (4u << (3 * u))) *reinterpret_cast<float4*>(T3 + R * P3 + ch) = xr[2][u];
       }
       if (!MIXED) {
         kbc[0][r1][r2] = vr[0]; kbc[1][r1][r2] = vr[1]; kbc[2][r1][r2] = vr[2];
