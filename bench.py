@@ -561,14 +561,35 @@ def run_domain(args):
     t_gen = time.time() - t_gen
     nbas, nocc = dom["nbas"], dom["nocc"]
     K = max(1, args.steps)
-    blocks = step_blocks(nocc, K)
     ntr = [ntrip(c, nocc) for c in CASES]
     N_all = sum(ntr)
+    # the triplets the steps compute: the whole domain, or a seeded sample of
+    # --triplet-sample per case (domains too large to time whole)
+    sampled = args.triplet_sample > 0
+    universe = (sample_triplets(nocc, args.triplet_sample, seed=23) if sampled
+                else [np.arange(n, dtype=np.int64) for n in ntr])
+    nun = [len(u) for u in universe]
+    blocks = [[universe[ci][nun[ci] * st // K:nun[ci] * (st + 1) // K] for ci in range(4)]
+              for st in range(K)]
+    bpos = [[(nun[ci] * st // K, nun[ci] * (st + 1) // K) for ci in range(4)] for st in range(K)]
+
+    def positions(per_case, seed):
+        # seeded positions within the universe, per case
+        out = []
+        for ci in range(4):
+            n = nun[ci]
+            if n == 0 or per_case == 0:
+                out.append(np.zeros(0, dtype=np.int64))
+                continue
+            rng = np.random.default_rng(seed + ci)
+            out.append(np.sort(rng.choice(n, size=min(per_case, n), replace=False)))
+        return out
 
     # CPU baseline (rank 0, single GPU only): the oracle on a bounded sample
     cpu = None
     oracle_vals = None
-    sel_cpu = sample_triplets(nocc, args.cpu_sample)
+    pos_cpu = positions(args.cpu_sample, 7)
+    sel_cpu = [universe[ci][pos_cpu[ci]] for ci in range(4)]
     if rank == 0 and world == 1 and args.cpu_sample > 0:
         oracle_vals, sec, flops, cores = cpu_oracle_sample(dom, sel_cpu, args.cpu_seconds)
         nor = sum(len(v) for v in oracle_vals.values())
@@ -583,22 +604,22 @@ def run_domain(args):
                   t2bb=dd["t2aa"])
     # the context keeps the domain's DF blocks and contraction operands
     # between the steps (built once, for all triplets, by the first step)
-    ctx = lno_ot.Context(local, args.precision, keep_operands=not args.no_keep)
-    alg = total_alg_flops(nocc, nbas)
-    # per-triplet contributions of the whole domain, written block by block
-    et = [torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in ntr]
+    ctx = lno_ot.Context(local, args.precision, keep_operands=not (args.no_keep or sampled))
+    alg = sum(alg_flops_triplet(c, nocc, nbas) * nun[ci] for ci, c in enumerate(CASES))
+    # per-triplet contributions of the computed triplets, written block by block
+    et = [torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in nun]
     eorb = ([torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in nocc]
             if args.fov else None)
 
-    def views(sel):
-        return [et[ci][sel[ci][0]:sel[ci][-1] + 1] if len(sel[ci]) else None
-                for ci in range(4)]
+    def views(st):
+        return [et[ci][bpos[st][ci][0]:bpos[st][ci][1]] if bpos[st][ci][1] > bpos[st][ci][0]
+                else None for ci in range(4)]
 
     def step(st, **kw):
         sel = blocks[st % K]
-        if args.closed_shell and K == 1:   # whole domain: the spin-flip shortcut applies
-            return ctx.energy(dd, e_trip=views(sel), e_orb=eorb, **kw)
-        return ctx.energy(dd, e_trip=views(sel), trip_sel=sel, e_orb=eorb, **kw)
+        if args.closed_shell and K == 1 and not sampled:   # whole domain: spin-flip shortcut
+            return ctx.energy(dd, e_trip=views(st % K), e_orb=eorb, **kw)
+        return ctx.energy(dd, e_trip=views(st % K), trip_sel=sel, e_orb=eorb, **kw)
 
     for w in range(args.warmup):
         step(w)
@@ -633,13 +654,13 @@ def run_domain(args):
     clocks = clk.summary()
     e_case = {c: math.fsum(o[c] for o in outs) for c in CASES}
     e_case["total"] = math.fsum(e_case[c] for c in CASES)
-    et_host = [x[:n].cpu().numpy() for x, n in zip(et, ntr)]
+    et_host = [x[:n].cpu().numpy() for x, n in zip(et, nun)]   # in universe order
 
     parity = None
     if oracle_vals is not None:
         errs = []
         for ci, c in enumerate(CASES):
-            for q, ref in zip(sel_cpu[ci], oracle_vals[c]):
+            for q, ref in zip(pos_cpu[ci], oracle_vals[c]):
                 errs.append(abs(float(et_host[ci][int(q)]) - ref))
         parity = {"sampled_triplets": len(errs), "max_abs_dE_per_triplet_Eh": max(errs),
                   "tolerance_Eh": 1e-8, "vs": "CPU oracle"}
@@ -681,7 +702,8 @@ def run_domain(args):
 
     # plain FP64 GPU path on a seeded triplet sample (same domain, same GPU)
     fp64, e64, accuracy_fp64 = None, None, None
-    fsel = sample_triplets(nocc, args.fp64_sample, seed=11)
+    pos64 = positions(args.fp64_sample, 11)
+    fsel = [universe[ci][pos64[ci]] for ci in range(4)]
     if args.fp64_sample > 0:
         c64 = lno_ot.Context(local, "fp64")
         et64 = [torch.zeros(max(len(x), 1), dtype=torch.float64, device=dev) for x in fsel]
@@ -698,7 +720,7 @@ def run_domain(args):
                           f"case); value = contraction + energy kernels, value_whole_call adds "
                           f"its float64 DF assembly of the orbitals the sample uses",
                 "speedup_of_timed_precision": value / world / v64}
-        d = [et_host[ci][fsel[ci]] - e64[ci] for ci in range(4)]
+        d = [et_host[ci][pos64[ci]] - e64[ci] for ci in range(4)]
         fp64["timed_precision_minus_fp64_per_triplet"] = err_stats(np.concatenate(d))
         # domain-total error of the timed precision from the sample, per case:
         # bias N_c mean_c (its 1-sigma uncertainty N_c sd_c / sqrt(n_c)) and the
@@ -729,12 +751,12 @@ def run_domain(args):
     accuracy = None if fp64 is None else {"vs_fp64_sample": accuracy_fp64}
     if args.ref_precision != "none" and args.precision != args.ref_precision:
         cref = lno_ot.Context(local, args.ref_precision)
-        etr = [torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in ntr]
+        etr = [torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in nun]
         t0 = time.perf_counter()
-        outr = cref.energy(dd, e_trip=etr)
+        outr = cref.energy(dd, e_trip=etr, trip_sel=universe if sampled else None)
         t_ref = time.perf_counter() - t0
         cref.close()
-        etr_h = [x[:n].cpu().numpy() for x, n in zip(etr, ntr)]
+        etr_h = [x[:n].cpu().numpy() for x, n in zip(etr, nun)]
         diff = {c: math.fsum((et_host[ci] - etr_h[ci]).tolist()) for ci, c in enumerate(CASES)}
         dtot = math.fsum(diff.values())
         accuracy = dict(accuracy or {})
@@ -742,9 +764,9 @@ def run_domain(args):
                     "reference_energy_Eh": outr["total"],
                     "timed_minus_reference_Eh": {**diff, "total": dtot},
                     "max_abs_per_triplet_Eh": float(max(np.abs(et_host[ci] - etr_h[ci]).max()
-                                                        for ci in range(4) if ntr[ci]))})
+                                                        for ci in range(4) if nun[ci]))})
         if e64 is not None:
-            dr = np.concatenate([etr_h[ci][fsel[ci]] - e64[ci] for ci in range(4)])
+            dr = np.concatenate([etr_h[ci][pos64[ci]] - e64[ci] for ci in range(4)])
             stt = err_stats(dr)
             # the reference's own domain-total error, from the float64 sample:
             # N (|mean| + 3 sd / sqrt(n)) over all N triplets of the domain
@@ -775,6 +797,10 @@ def run_domain(args):
     mhz = clocks.get("sm_mhz") or 2070.0
     en_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     en_achieved = en_flops / (tot["ms_energy"] / 1e3) / 1e12
+    # its HBM floor: every restricted element reads three float32 intermediates
+    # once (X[a,(bc)], X[b,(ac)], X[c,(ab)]; mixed: Y twice and Z' once)
+    en_bytes = passes * 12.0 * (n_same + n_mixed)
+    en_gbs = en_bytes / (tot["ms_energy"] / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -787,15 +813,21 @@ def run_domain(args):
                                 f"naux={dom['naux']}, closed shell" if args.closed_shell
                                 else workload_name(args.config))
                    + (" + f_ov (RO reference)" if args.fov else "")
-                   + f"; the {K} timed steps compute the whole domain once (step s: block s "
-                     f"of {K} of every spin case's restricted triplets; the first step also "
-                     f"stages the domain and builds its DF blocks and contraction operands, "
-                     f"which the context keeps for the later steps)",
+                   + (f"; the {K} timed steps compute a seeded sample of {args.triplet_sample} "
+                      f"triplets per spin case once (block s of {K} of each case's sample)"
+                      if sampled else
+                      f"; the {K} timed steps compute the whole domain once (step s: block s "
+                      f"of {K} of every spin case's restricted triplets; the first step also "
+                      f"stages the domain and builds its DF blocks and contraction operands, "
+                      f"which the context keeps for the later steps)"),
                    **cfg_public(cfg), **({"fov_sd": 0.02} if args.fov else {}),
                    "triplets": dict(zip(CASES, ntr)),
+                   **({"timed_triplet_sample": dict(zip(CASES, nun)),
+                       "sample_flop_fraction": alg / total_alg_flops(nocc, nbas)}
+                      if sampled else {}),
                    "l2": f"inputs larger than L2 ({domain_bytes(nbas, nocc, dom['naux']) / 1e9:.1f} GB)",
                    "parallelism": f"replicas x{world} (one domain per GPU)"},
-        "domains_per_s": world / (ms_max / 1e3),
+        "domains_per_s": None if sampled else world / (ms_max / 1e3),
         "energy_Eh": e_case,
         "accuracy": accuracy,
         "parity": parity,
@@ -807,11 +839,15 @@ def run_domain(args):
                      "per_launch": {"ms": tc_launch_ms, "tensor_flops": tc_flops_launch,
                                     "launches": nlaunch}},
         "roofline_energy": {"kernel": "energy_f32 (W/V assembly, W(W+V)/D, sums)",
-                            "bound": "alu", "achieved": en_achieved, "peak": en_peak,
-                            "unit": "TFLOP/s (FP32)", "frac": en_achieved / en_peak,
-                            "elements": n_same + n_mixed, "passes": passes,
-                            "elements_per_s": passes * (n_same + n_mixed) / (tot["ms_energy"] / 1e3),
-                            "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock"},
+                            "bound": "hbm", "achieved": en_gbs, "peak": pk["hbm_gbs"],
+                            "unit": "GB/s", "frac": en_gbs / pk["hbm_gbs"],
+                            "algorithmic_bytes": en_bytes,
+                            "bytes_per_element": 12, "elements": n_same + n_mixed,
+                            "passes": passes, "peak_source": f"{pk['source']} copy bandwidth",
+                            "alu": {"achieved": en_achieved, "peak": en_peak,
+                                    "unit": "TFLOP/s (FP32)", "frac": en_achieved / en_peak,
+                                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM "
+                                                   "clock"}},
         "breakdown_ms": {"ms_total": tot["ms_total"], "ms_stage": tot["ms_stage"],
                          "ms_contract": tot["ms_contract"], "ms_energy": tot["ms_energy"]},
         "gpu_launches": int(launches),
@@ -847,6 +883,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--fp64-sample", type=int, default=64, help="FP64-path triplets per case")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--triplet-sample", type=int, default=0,
+                    help="time a seeded sample of this many triplets per case instead of the "
+                         "whole domain (for domains too large to time whole, e.g. c2)")
     ap.add_argument("--no-keep", action="store_true",
                     help="every step builds its own operands (no keep_operands)")
     ap.add_argument("--closed-shell", action="store_true",

@@ -1111,8 +1111,9 @@ struct SpinPass {
       if (e1) cudaEventRecord(e1, R.st);
       if (e0 && e1) R.energy_ev.push_back({e0, e1});
       R.stats->energy_launches += 2;
-      // the host reuses pf/pt for the next group: make sure the copy is done
-      CU(cudaStreamSynchronize(R.st));
+      // no host sync: the next group's descriptors overwrite pf/pt only after
+      // cudaMemcpyAsync has staged this group's (pageable source), and the
+      // device array is reused in stream order after this group's kernels
     }
     return LNO_OT_OK;
   }
