@@ -497,17 +497,20 @@ def run_naf(args):
                    "naux_kept": comp_h["naux"]}
     c64.close()
     del comp
-    ctx = lno_ot.Context(0, args.precision)
-    e_full = ctx.energy(dd)["total"]
-    e_half = ctx.energy(comp_h)["total"]
-    ctx.close()
+    e_full = e_half = None
+    if dom["nbas"] <= 200:   # E(T) of the full and the compressed domain (small domains)
+        ctx = lno_ot.Context(0, args.precision)
+        e_full = ctx.energy(dd)["total"]
+        e_half = ctx.energy(comp_h)["total"]
+        ctx.close()
     line = {"metric": "NAF compression (eq naf_w) seconds and E(T) change", "unit": "s",
             "value": out["1e-2"]["seconds"], "higher_is_better": False, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(args.config), **cfg_public(cfg)},
             "naux": dom["naux"], "eigenvalues": {"max": float(lam[0]), "min": float(lam[-1])},
             "runs": out, "E_full_Eh": e_full, "E_half_naf_Eh": e_half,
-            "dE_half_Eh": e_half - e_full, "energy_precision": args.precision}
+            "dE_half_Eh": None if e_full is None else e_half - e_full,
+            "energy_precision": args.precision}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -604,7 +607,8 @@ def run_domain(args):
                   t2bb=dd["t2aa"])
     # the context keeps the domain's DF blocks and contraction operands
     # between the steps (built once, for all triplets, by the first step)
-    ctx = lno_ot.Context(local, args.precision, keep_operands=not (args.no_keep or sampled))
+    ctx = lno_ot.Context(local, args.precision, keep_operands=not (args.no_keep or sampled),
+                         tune_cache=args.tune)
     alg = sum(alg_flops_triplet(c, nocc, nbas) * nun[ci] for ci, c in enumerate(CASES))
     # per-triplet contributions of the computed triplets, written block by block
     et = [torch.zeros(max(n, 1), dtype=torch.float64, device=dev) for n in nun]
@@ -886,6 +890,8 @@ def main():
     ap.add_argument("--triplet-sample", type=int, default=0,
                     help="time a seeded sample of this many triplets per case instead of the "
                          "whole domain (for domains too large to time whole, e.g. c2)")
+    ap.add_argument("--tune", default=None,
+                    help="tuning table (vmax bn group_cap lines) for the timed context")
     ap.add_argument("--no-keep", action="store_true",
                     help="every step builds its own operands (no keep_operands)")
     ap.add_argument("--closed-shell", action="store_true",

@@ -100,8 +100,9 @@ typedef struct {
                              (paper_2311_10048_gb300/tune.py): text lines
                              "vmax bn group_cap" giving, per bucket of
                              virtual-space size, the tile width of the W
-                             contraction (64, 128 or 256 where the precision
-                             has that variant; 0 = its default) and the cap
+                             contraction (64, 96, 128 or 256 where the
+                             precision has that variant; 0 = its default) and
+                             the cap
                              on triplets per contraction launch.  Lines
                              starting with '#' are comments.  Unreadable
                              file: lno_ot_init returns LNO_OT_EINVAL. */

@@ -242,7 +242,7 @@ struct Operand {
   int esz = 2;                   // bytes per slice element
   int S = 0;
   int64_t slice_stride = 0;
-  CUtensorMap map128, map256, map64;  // TMA maps with boxes of 128 (A role, B of BN 128), 256, 64 rows
+  CUtensorMap map128, map256, map96, map64;  // TMA maps with boxes of 128 (A role, B of BN 128), 256, 96, 64 rows
   int64_t total_rows() const { return (int64_t)nslot * rows; }
 };
 
@@ -252,13 +252,13 @@ int contract_bn(int S, int bn) {
   switch (S) {
     case 2: return bn == 128 ? 128 : 256;
     case 3: return bn == 64 ? 64 : 128;
-    case 4: return bn == 64 ? 64 : 128;
+    case 4: return bn == 64 ? 64 : bn == 96 ? 96 : 128;
     default: return 64;
   }
 }
 
 const CUtensorMap& map_for(const Operand& op, int box) {
-  return box == 256 ? op.map256 : box == 64 ? op.map64 : op.map128;
+  return box == 256 ? op.map256 : box == 96 ? op.map96 : box == 64 ? op.map64 : op.map128;
 }
 
 // One grouped W-contraction launch with float32 output.
@@ -280,7 +280,7 @@ cudaError_t launch_contract(int S, bool tf, int bn_req, const Operand& A0, const
                                                      nullptr, nsm, st, dg);
   if (S == 2) return bn == 128 ? LNO_CALL(2, 128) : LNO_CALL(2, 256);
   if (S == 3) return bn == 64 ? LNO_CALL(3, 64) : LNO_CALL(3, 128);
-  if (S == 4) return bn == 64 ? LNO_CALL(4, 64) : LNO_CALL(4, 128);
+  if (S == 4) return bn == 64 ? LNO_CALL(4, 64) : bn == 96 ? LNO_CALL(4, 96) : LNO_CALL(4, 128);
   return LNO_CALL(5, 64);
 #undef LNO_CALL
 }
@@ -355,6 +355,7 @@ struct Run {
       TRY(make_operand_map(&op.map128, base, op.Kp, rows_, op.S, op.slice_stride, 128, op.esz));
       TRY(make_operand_map(&op.map256, base, op.Kp, rows_, op.S, op.slice_stride, 256, op.esz));
       TRY(make_operand_map(&op.map64, base, op.Kp, rows_, op.S, op.slice_stride, 64, op.esz));
+      TRY(make_operand_map(&op.map96, base, op.Kp, rows_, op.S, op.slice_stride, 96, op.esz));
     }
     return LNO_OT_OK;
   }

@@ -31,7 +31,8 @@
 //   warp 0      TMA producer (one thread), STAGES-deep smem ring
 //   warp 1      TMEM allocator and MMA issuer (one thread); S accumulators
 //               of 128 x BN FP32 (S * BN <= 512 TMEM columns: BN = 256 or 128
-//               for S = 2, 128 or 64 for S = 3, 4, and 64 for S = 5)
+//               for S = 2, 128 or 64 for S = 3, 128, 96 or 64 for S = 4, and 64
+//               for S = 5)
 //   warps 2..5  epilogue: tcgen05.ld -> scale -> coalesced stores along m; when
 //               TMEM has room ((S + 1) BN <= 512) the combined tile is parked in
 //               spare columns so the next tile's MMAs overlap the stores
@@ -560,6 +561,7 @@ LNO_TC_INST(2, 128, float)
 LNO_TC_INST(3, 128, float)
 LNO_TC_INST(3, 64, float)
 LNO_TC_INST(4, 128, float)
+LNO_TC_INST(4, 96, float)
 LNO_TC_INST(4, 64, float)
 LNO_TC_INST(5, 64, float)
 LNO_TC_INST(1, 256, float)

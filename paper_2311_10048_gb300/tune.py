@@ -17,7 +17,7 @@ import time
 
 BUCKETS = (96, 160, 224, 320, 448)          # vmax of each bucket
 # contraction tile widths the library has per precision (S * BN <= 512 TMEM columns)
-TILE_WIDTHS = {"bf16x3": (256, 128), "bf16x6": (128, 64), "bf16x10": (128, 64),
+TILE_WIDTHS = {"bf16x3": (256, 128), "bf16x6": (128, 64), "bf16x10": (128, 96, 64),
                "bf16x15": (64,)}
 GROUP_CAPS = (16, 64)
 

@@ -253,13 +253,13 @@ def test_shapes_bf16x10_vs_oracle(ctx10, shape):
 
 
 @pytest.mark.parametrize("prec,widths", [("bf16x3", (256, 128)), ("bf16x6", (128, 64)),
-                                         ("bf16x10", (128, 64))])
+                                         ("bf16x10", (128, 64)), ("bf16x10", (128, 96))])
 def test_tile_widths_give_bitwise_equal_results(lib, tmp_path, prec, widths):
     # several n-tiles per problem (154 virtuals: 11781 pairs) and a ragged m edge
     d = lno_ot.to_device(make_domain(160, (6, 4), naux=120, L=30.0, seed=2))
     res = []
     for bn in widths:
-        p = tmp_path / f"t{bn}.txt"
+        p = tmp_path / f"t{prec}{bn}.txt"
         p.write_text(f"100000 {bn} 16\n")
         ctx = lno_ot.Context(0, prec, tune_cache=str(p))
         res.append(ctx.energy(d))
