@@ -134,6 +134,51 @@ def test_c0_gradient_vs_oracle_and_central_differences(ctx64):
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (key, fd, an)
 
 
+def test_c4_subset_central_differences_all_nine_inputs(ctx64):
+    # at the differentiation domain's size (nbas 200, 20/18 occupied): the
+    # adjoint on a seeded triplet subset against central differences of the
+    # float64 forward on the same subset, h = 1e-5, along one random
+    # symmetry-respecting direction per input
+    d = config_domain("c4")
+    rng = np.random.default_rng(2024)
+    na, nb = d["nocc"]
+    sel = [np.sort(rng.choice(T.n_triplets(c, na, nb), size=2, replace=False)).astype(np.int64)
+           for c in CASES]
+    g, _ = gpu_grad(ctx64, d, sel)
+    dd = lno_ot.to_device(d)
+    h = 1e-5
+
+    def E(dm):
+        return ctx64.energy(dm, trip_sel=sel)["total"]
+
+    def perturbed(key, x, sign):
+        dm = dict(dd, B=list(dd["B"]), eps=list(dd["eps"]), t1=list(dd["t1"]))
+        xt = torch.as_tensor(x, device="cuda")
+        if key in ("B0", "B1"):
+            s = int(key[1]); dm["B"][s] = dd["B"][s] + sign * h * xt
+        elif key in ("e0", "e1"):
+            s = int(key[1]); dm["eps"][s] = dd["eps"][s] + sign * h * xt
+        elif key in ("t10", "t11"):
+            s = int(key[2]); dm["t1"][s] = dd["t1"][s] + sign * h * xt
+        else:
+            dm[key] = dd[key] + sign * h * xt
+        return dm
+
+    shapes = {"B0": d["B"][0].shape, "B1": d["B"][1].shape, "e0": d["eps"][0].shape,
+              "e1": d["eps"][1].shape, "t10": d["t1"][0].shape, "t11": d["t1"][1].shape,
+              "t2aa": d["t2aa"].shape, "t2bb": d["t2bb"].shape, "t2ab": d["t2ab"].shape}
+    for ki, key in enumerate(KEYS):
+        x = rng.standard_normal(shapes[key])
+        if key in ("B0", "B1"):
+            x = x + x.transpose(0, 2, 1)
+        if key in ("t2aa", "t2bb"):
+            x = x - x.transpose(1, 0, 2, 3)
+            x = x - x.transpose(0, 1, 3, 2)
+        fd = (E(perturbed(key, x, +1)) - E(perturbed(key, x, -1))) / (2 * h)
+        an = float((g[ki] * torch.as_tensor(x)).sum())
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (key, fd, an)
+
+
 def test_c4_subset_gradient_vs_oracle(ctx64):
     d = config_domain("c4")
     na, nb = d["nocc"]
