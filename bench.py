@@ -361,6 +361,10 @@ def run_c3(args):
         "energies_Eh": {int(k): v for k, v in sorted(energies.items())},
         "breakdown_ms_rank0": {k: stats[k] for k in ("ms_total", "ms_stage", "ms_contract",
                                                      "ms_energy")},
+        "contraction_tflops_per_launch_rank0": (stats["tensor_flops"] / stats["ms_contract"] / 1e9
+                                                if stats["ms_contract"] > 0 else None),
+        "energy_elements_per_s_rank0": (stats["elements"] / stats["ms_energy"] * 1e3
+                                        if stats["ms_energy"] > 0 else None),
         "gpu_launches": int(stats["contract_launches"] + stats["energy_launches"]
                             + stats["other_launches"]),
         "clocks": clk.summary(),
@@ -373,8 +377,10 @@ def run_c3(args):
 
 
 def run_backward(args):
-    """Adjoint timing: lno_ot_backward (float64, W recomputed per triplet) on a
-    seeded triplet sample of the domain, against its forward on the same sample."""
+    """Adjoint timing: lno_ot_backward (W recomputed per triplet) on a seeded
+    triplet sample of the domain, against its forward on the same sample, both
+    in --precision (a tensor-core precision runs the adjoint's contractions on
+    the tensor cores, float64 runs them in float64)."""
     import torch
     from paper_2311_10048_gb300 import lno_ot
     cfg = dict(CONFIGS[args.config])
@@ -383,7 +389,7 @@ def run_backward(args):
     sel = sample_triplets(nocc, args.bwd_sample, seed=13)
     dev = torch.device("cuda", 0)
     dd = lno_ot.to_device(dom, dev)
-    ctx = lno_ot.Context(0, "fp64")
+    ctx = lno_ot.Context(0, args.precision)
     g = dict(dB=[torch.empty_like(dd["B"][0]), torch.empty_like(dd["B"][1])],
              deps=[torch.empty_like(dd["eps"][0]), torch.empty_like(dd["eps"][1])],
              dt1=[torch.empty_like(dd["t1"][0]), torch.empty_like(dd["t1"][1])],
@@ -404,7 +410,11 @@ def run_backward(args):
     ntr = sum(len(x) for x in sel)
     flops = sum(alg_flops_triplet(c, nocc, nbas) * len(sel[ci]) for ci, c in enumerate(CASES))
     line = {"metric": "E(T) adjoint (dE/dB, deps, dT1, dT2) wall time on a triplet sample",
-            "value": t_bwd, "unit": "s", "higher_is_better": False, "dtype": "f64",
+            "value": t_bwd, "unit": "s", "higher_is_better": False,
+            "dtype": "f64" if args.precision == "fp64" else "bf16",
+            "precision": args.precision,
+            "adjoint_contractions": ("float64 CUDA cores" if args.precision == "fp64" else
+                                     "tensor cores, 4 exact BF16 slices, float64 output"),
             "data": "synthetic", "steps": 1, "warmup": 1,
             "config": {"workload": workload_name(args.config) + " (adjoint)", **cfg_public(cfg),
                        "sample": f"{ntr} seeded triplets ({', '.join(f'{c}:{len(sel[i])}' for i, c in enumerate(CASES))})"},

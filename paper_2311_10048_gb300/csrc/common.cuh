@@ -73,7 +73,12 @@ struct EnergyArgs {
   int64_t x_stride;    // elements between consecutive triplets' XT (or YT)
   int64_t z_stride;    // between consecutive ZT
   const Trip* trips;   // [ntrip]
-  double* partial;     // [ntrip][gridDim.x]
+  double* partial;     // float64 path: [ntrip][gridDim.x]; float32 path: [ntrip][nchunk][8]
+  // float32 path: the tiles of a triplet are split into nchunk items
+  // (chunk c: tiles c, c + nchunk, ...); nitems = ntrip * nchunk items run on a
+  // persistent grid of at most (resident CTAs per SM) * nsm CTAs
+  int nchunk, nitems, nsm;
+  int* flag;           // device error flag (bounded waits of the TMA-staged variant)
   // Laplace form (Sec. 3.7, eq laplace_transform): with lap_w != 0 the
   // kernels weight each element by -lap_w exp(lap_s D) instead of 1/D (one
   // quadrature point of 1/D = -sum_q w_q exp(s_q D), D < 0)
@@ -125,8 +130,8 @@ struct TcSeg {
 struct TcProb {
   TcSeg seg[kMaxSeg];
   int nseg;
-  int pad_;
-  void* out;        // XT base of this problem (float or double), [N][ldo]
+  int accum;        // float64 transposed output only: 1 adds to out instead of storing
+  void* out;        // output of this problem: [N][ldo] (transposed) or [M][ldo] (row-major)
 };
 
 // Bounded-wait settings of one contraction launch: wait_cycles limits every
@@ -138,8 +143,9 @@ struct TcDiag {
 };
 
 // tc_gemm.cu: grouped sliced contraction.  mA: maps with 128-row boxes,
-// mB: maps with BN-row boxes; instances (S, BN, OutT) are listed there.
-template <int S, int BN, typename OutT, bool TF = false>
+// mB: maps with BN-row boxes; instances (S, BN, OutT, TF, RM) are listed there
+// (RM: row-major output out[m][n], else the transposed out[n][m]).
+template <int S, int BN, typename OutT, bool TF = false, bool RM = false>
 cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
                            int nprob, int M, int N, int ldo, double scale, int* flag,
                            unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag);
@@ -147,6 +153,8 @@ long long tc_default_wait_cycles();
 inline TcDiag tc_normal() { return TcDiag{tc_default_wait_cycles(), 0}; }
 int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
                      int64_t slice_stride, int box_rows, int esz = 2);
+int make_f32_map(CUtensorMap* map, const void* base, int rank, const int64_t* dims,
+                 const int64_t* strides, const int* box, bool sw64);
 int sliced_product_bn(int S);
 cudaError_t launch_sliced_product(int S, const CUtensorMap* mA, const CUtensorMap* mB,
                                   const TcProb* dp, int M, int N, double scale, int* flag,

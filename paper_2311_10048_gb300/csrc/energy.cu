@@ -20,7 +20,10 @@
 // the quotient is correctly rounded, 16 elements are summed in float32 and
 // every such partial is added in float64 (all roundings to nearest, so no
 // systematic bias builds up over the ~1e12 elements of a large domain).
+#include <algorithm>
+
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace lno {
 
@@ -394,16 +397,34 @@ __device__ __forceinline__ float lap_factor(float shi, float slo, float D) {
 // FU (mixed spin only): V = V(T1) + V(f_ov) in one pass; the f_ov planes sit
 // vt_half floats after the T1 planes of each triplet's table and the f_ov
 // coefficients come from a.fs / a.ft.
-template <bool MIXED, bool FM, bool FU, bool LAP>
+// TM (mixed spin only): the three sub-cubes come by TMA into a two-stage ring
+// in dynamic shared memory (tile i in stage i & 1, issued two tiles ahead by
+// thread 0, completion on one mbarrier per stage) instead of through
+// registers:
+//   T1[b][c][a]  one 16x16x16 box of the 4-D map (a, c, b, triplet) over Y,
+//                64-byte rows with the 64-byte swizzle (16-byte chunk
+//                index XOR (row >> 1) & 3)
+//   T2[a][c][b]  the same map at (b0, c0, a0)
+//   T3[b][a][C]  16 boxes of 16 rows of the 3-D map (C, pair row, triplet)
+//                over Z', one per b (rows (a0..a0+15, b) are consecutive)
+template <bool MIXED, bool FM, bool FU, bool LAP, bool TM>
 __global__ void __launch_bounds__(256, 2)
 energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ Z,
-           const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt, int64_t vt_half) {
+           const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt, int64_t vt_half,
+           const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapZ) {
   static_assert(!FU || (MIXED && !FM), "the fused f_ov pass is the mixed-spin W (W + V) sum");
+  static_assert(!TM || (MIXED && !FU), "TMA staging: mixed spin without the fused f_ov pass");
   constexpr int P1 = 20, P2 = 18, P3 = 24;
   constexpr int FT = FU ? TB : 1, FP = FU ? TP : 1;   // f_ov table sizes (1 when absent)
-  __shared__ __align__(16) float T1[TB * TB * P1];
-  __shared__ __align__(16) float T2[TB * TB * P2];
-  __shared__ __align__(16) float T3[TB * TB * P3];
+  constexpr int CUBE = TB * TB * TB;                   // floats of one sub-cube
+  __shared__ __align__(16) float T1[TM ? 4 : TB * TB * P1];
+  __shared__ __align__(16) float T2[TM ? 4 : TB * TB * P2];
+  __shared__ __align__(16) float T3[TM ? 4 : TB * TB * P3];
+  extern __shared__ unsigned char dsm_raw[];
+  // TM ring: stage s at ring + 3 CUBE s (T1, T2, T3), then two mbarriers
+  float* const ring = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* const fullb = reinterpret_cast<uint64_t*>(ring + 6 * CUBE);
   __shared__ __align__(16) float4 kac[TB][TB];
   __shared__ __align__(16) float4 kab[TB][TB];
   __shared__ float kbc[3][TB][TP];
@@ -411,7 +432,6 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   __shared__ float ael[TB];
   __shared__ float tb_s[3][TB], tc_s[3][TB];
   __shared__ float ebh[2][TB], ebl[2][TB];
-  __shared__ double red[8];
   // f_ov planes (b,C): t^{bC}_{jK}, t^{bC}_{iK}; (a,C): t^{aC}_{jK}, t^{aC}_{iK};
   // (a,b): t^{ab}_{ij}; coefficients f_ia, f_ja / f_ib, f_jb / f_KC
   __shared__ float kbcf[2][FT][FP];
@@ -420,12 +440,14 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   __shared__ __align__(8) float2 adf[FT];
   __shared__ float tbf_s[2][FT], tcf_s[FT];
 
-  const int g = blockIdx.y;
-  const Trip tr = a.trips[g];
-  const float* Xg = X + (int64_t)g * a.x_stride;
-  const float* Zg = MIXED ? Z + (int64_t)g * a.z_stride : nullptr;
-  const float* Vg = VT + (int64_t)g * vt_stride;
-  const float* Vf = Vg + vt_half;
+  // Persistent item loop: item w = g * P + chunk (P = a.nchunk) covers the
+  // tiles chunk, chunk + P, ... of triplet g; CTA b takes items b, b + grid,
+  // ...  Each item's sum is formed in a fixed order and written as one
+  // float64 partial per warp, so results do not depend on the grid size.
+  const int P = a.nchunk;
+  int w = blockIdx.x;
+  if (w >= a.nitems) return;
+  int g = w / P;
   const int tid = threadIdx.x;
   const int r1 = tid / TB, r2 = tid % TB;           // row owned in the fetch phase
   const int lane = tid & 31, wid = tid >> 5;
@@ -433,8 +455,12 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   const int bl0 = 2 * (((wid & 3) << 1) | (lane >> 4));   // first of the b pair
   const int al0 = 8 * (wid >> 2);                    // a half
   const int nvs = a.nvs, nvt = a.nvt;
-  const TwoF eocc = split_df(MIXED ? a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_t[tr.k]
-                                   : a.eps_s[tr.i] + a.eps_s[tr.j] + a.eps_s[tr.k]);
+  auto occ_sum = [&](int gg) {
+    const Trip t = a.trips[gg];
+    return split_df(MIXED ? a.eps_s[t.i] + a.eps_s[t.j] + a.eps_t[t.k]
+                          : a.eps_s[t.i] + a.eps_s[t.j] + a.eps_s[t.k]);
+  };
+  TwoF eocc = occ_sum(g);
   const float lshi = (float)a.lap_s;                          // Laplace s (LAP only)
   const float lslo = (float)(a.lap_s - (double)lshi);
 
@@ -450,13 +476,20 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   // the 16-byte chunk (t & 3) of sub-cube row R = 64 u + (t >> 2), so four
   // neighbouring lanes read one 64-byte row and a warp reads 8 whole rows per
   // load instruction.  okm bit (3 u + cube) marks the valid rows.
-  auto fetch = [&](int q) {
+  auto fetch = [&](int gq, int q) {
+    const Trip tr = a.trips[gq];
+    const float* Xg = X + (int64_t)gq * a.x_stride;
+    const float* Zg = MIXED ? Z + (int64_t)gq * a.z_stride : nullptr;
+    const float* Vg = VT + (int64_t)gq * vt_stride;
+    const float* Vf = Vg + vt_half;
+    (void)Zg;
+    (void)Vf;
     const int3 blk = a.blocks[q];
     const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
     const int ch = (tid & 3) * 4;
     okm = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < (TM ? 0 : 4); ++u) {
       const int R = 64 * u + (tid >> 2);
       const int s1 = R >> 4, s2 = R & 15;
       const float4* p1 = nullptr;
@@ -558,16 +591,70 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   };
 
   TwoF acc = {0.f, 0.f};
-  int q = blockIdx.x;
-  if (q < a.nblocks) fetch(q);
-  for (; q < a.nblocks; q += gridDim.x) {
+  int q = w - g * P;
+  // TM: the producer cursor (pw, pg, pq) runs two tiles ahead of (w, g, q)
+  auto advance = [&](int& cw, int& cg, int& cq) {
+    cq += P;
+    if (cq >= a.nblocks) {
+      cw += (int)gridDim.x;
+      cg = cw / P;
+      cq = cw - cg * P;
+    }
+  };
+  auto issue = [&](int cg, int cq, int st) {
+    const int3 bk = a.blocks[cq];
+    const int a0 = bk.x * TB, b0 = bk.y * TB, c0 = bk.z * TB;
+    const uint32_t bar = smem_u32(fullb + st);
+    float* base = ring + 3 * CUBE * st;
+    mbar_expect_tx(bar, 3u * CUBE * 4u);
+    tma_load_4d(smem_u32(base), &mapX, bar, a0, c0, b0, cg);
+    tma_load_4d(smem_u32(base + CUBE), &mapX, bar, b0, c0, a0, cg);
+#pragma unroll 1
+    for (int bl = 0; bl < TB; ++bl)
+      tma_load_3d(smem_u32(base + 2 * CUBE + bl * TB * TB), &mapZ, bar, c0,
+                  (int)pair_index(a0, b0 + bl), cg);
+  };
+  int pw = w, pg = g, pq = q, issued = 0;
+  uint32_t it = 0;   // tiles of this CTA so far
+  const float* cur = ring;
+  if constexpr (TM) {
+    if (tid == 0) {
+      mbar_init(smem_u32(fullb), 1);
+      mbar_init(smem_u32(fullb + 1), 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int st = 0; st < 2 && pw < a.nitems; ++st) {
+      if (tid == 0) issue(pg, pq, st);
+      ++issued;
+      advance(pw, pg, pq);
+    }
+  }
+  fetch(g, q);
+  for (;;) {
     const int3 blk = a.blocks[q];
     const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
+    if constexpr (TM) {   // this tile's sub-cubes
+      const int st = (int)(it & 1u);
+      const bool ok = mbar_wait_bounded(smem_u32(fullb + st), (it >> 1) & 1u, 4000000000LL);
+      if (__syncthreads_or(!ok)) {
+        // give up: record the error, let the copies in flight land, leave
+        if (tid == 0) {
+          atomicCAS(a.flag, 0, 7);
+          for (uint32_t j = it; j < (uint32_t)issued; ++j)
+            mbar_wait_bounded(smem_u32(fullb + (j & 1u)), (j >> 1) & 1u, 4000000000LL);
+        }
+        __syncthreads();
+        return;
+      }
+      cur = ring + 3 * CUBE * st;
+    }
     // ---- registers -> shared ----
     {
       const int ch = (tid & 3) * 4;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < (TM ? 0 : 4); ++u) {
         const int R = 64 * u + (tid >> 2);
         if (okm & (1u << (3 * u))) *reinterpret_cast<float4*>(T1 + R * P1 + ch) = xr[0][u];
         if (okm & (2u << (3 * u))) {
@@ -613,7 +700,15 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
       }
     }
     __syncthreads();
-    if (q + (int)gridDim.x < a.nblocks) fetch(q + gridDim.x);  // next tile in flight
+    // next tile (of this item, else the first of the CTA's next item) in flight
+    int wn = w, gn = g, qn = q + P;
+    if (qn >= a.nblocks) {
+      wn = w + (int)gridDim.x;
+      gn = wn / P;
+      qn = wn - gn * P;
+    }
+    const bool more = wn < a.nitems;
+    if (more) fetch(gn, qn);
     // ---- elements: (a in half, b pair, c) ----------------------------------
     {
       const int c = c0 + cl;
@@ -649,15 +744,29 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
           // chains interleave; the same-spin tiles keep the branches (more of
           // their elements are masked on the diagonal blocks)
           const int a4 = al0 + 4 * h;
-          const float4 q0 = *reinterpret_cast<const float4*>(x1r0 + a4);
-          const float4 q1 = *reinterpret_cast<const float4*>(x1r1 + a4);
+          float4 q0, q1;
+          if constexpr (TM) {   // swizzled 64-byte rows (b, c) of T1
+            const int ra = bl0 * TB + cl, rb = ra + TB;
+            q0 = *reinterpret_cast<const float4*>(cur + ra * TB + (((a4 >> 2) ^ ((ra >> 1) & 3)) << 2));
+            q1 = *reinterpret_cast<const float4*>(cur + rb * TB + (((a4 >> 2) ^ ((rb >> 1) & 3)) << 2));
+          } else {
+            q0 = *reinterpret_cast<const float4*>(x1r0 + a4);
+            q1 = *reinterpret_cast<const float4*>(x1r1 + a4);
+          }
           const float x1a[2][4] = {{q0.x, q0.y, q0.z, q0.w}, {q1.x, q1.y, q1.z, q1.w}};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int al = a4 + u;
             const float4 da = ad[al];
             const float del = ael[al];
-            const float2 x2 = *reinterpret_cast<const float2*>(T2 + (al * TB + cl) * P2 + bl0);
+            float2 x2;
+            if constexpr (TM) {   // swizzled 64-byte rows (a, c) of T2
+              const int r = al * TB + cl;
+              x2 = *reinterpret_cast<const float2*>(
+                  cur + CUBE + r * TB + ((((bl0 >> 2) ^ ((r >> 1) & 3)) << 2) | (bl0 & 3)));
+            } else {
+              x2 = *reinterpret_cast<const float2*>(T2 + (al * TB + cl) * P2 + bl0);
+            }
             const float4 vac = kac[al][cl];
             const float x2a[2] = {x2.x, x2.y};
             float2 daf = make_float2(0.f, 0.f), vacf = make_float2(0.f, 0.f);
@@ -669,7 +778,8 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
             for (int sb = 0; sb < 2; ++sb) {
               const int bl = bl0 + sb;
               const bool valid = rowok[sb] && a0 + al < b0 + bl;
-              const float x3 = T3[(al * TB + bl) * P3 + cl];
+              const float x3 = TM ? cur[2 * CUBE + (bl * TB + al) * TB + cl]
+                                  : T3[(al * TB + bl) * P3 + cl];
               const float vab = kab[al][bl].x;
               const float w = x1a[sb][u] - x2a[sb] + x3;
               float v = da.x * k0[sb] - da.y * k1[sb] - tb0[sb] * vac.x +
@@ -737,15 +847,25 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
       (void)tc2;
     }
     __syncthreads();
-  }
-  double dacc = (double)acc.hi + (double)acc.lo;
-  for (int off = 16; off > 0; off >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, off);
-  if ((tid & 31) == 0) red[tid >> 5] = dacc;
-  __syncthreads();
-  if (tid == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < 8; ++w) sum += red[w];
-    a.partial[(int64_t)g * gridDim.x + blockIdx.x] = LAP ? -a.lap_w * sum : sum;
+    if constexpr (TM) {   // stage it & 1 is free: the tile two ahead goes there
+      if (pw < a.nitems) {
+        if (tid == 0) issue(pg, pq, (int)(it & 1u));
+        ++issued;
+        advance(pw, pg, pq);
+      }
+      ++it;
+    }
+    if (wn != w) {   // item (g, w - g P) complete: one float64 partial per warp
+      double dacc = (double)acc.hi + (double)acc.lo;
+      for (int off = 16; off > 0; off >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, off);
+      if (lane == 0) a.partial[((int64_t)w * 8) + wid] = LAP ? -a.lap_w * dacc : dacc;
+      acc = {0.f, 0.f};
+      if (!more) break;
+      w = wn;
+      if (gn != g) eocc = occ_sum(gn);
+      g = gn;
+    }
+    q = qn;
   }
 }
 
@@ -754,19 +874,30 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
 __global__ void reduce_partials(const double* __restrict__ partial, int np,
                                 const double* __restrict__ partial2, int ntrip,
                                 double* __restrict__ e_trip) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per triplet: lane l sums p = l, l + 32, ... (Neumaier), then the
+  // lanes' (sum, compensation) pairs are combined in a fixed shuffle tree, so
+  // the result does not depend on timing
+  const int lane = threadIdx.x & 31;
+  const int g = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (g >= ntrip) return;
   double s = 0.0, c = 0.0;
   for (int half = 0; half < (partial2 ? 2 : 1); ++half) {
-    const double* src = half ? partial2 : partial;
-    for (int p = 0; p < np; ++p) {
-      double x = src[(int64_t)g * np + p];
-      double t = s + x;
+    const double* src = (half ? partial2 : partial) + (int64_t)g * np;
+    for (int p = lane; p < np; p += 32) {
+      const double x = src[p];
+      const double t = s + x;
       c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
       s = t;
     }
   }
-  e_trip[g] = s + c;
+  for (int off = 16; off > 0; off >>= 1) {
+    const double so = __shfl_down_sync(0xffffffffu, s, off);
+    const double co = __shfl_down_sync(0xffffffffu, c, off);
+    const double t = s + so;
+    c += (fabs(s) >= fabs(so) ? (s - t) + so : (so - t) + s) + co;
+    s = t;
+  }
+  if (lane == 0) e_trip[g] = s + c;
 }
 
 // Orbital contributions of eq cim_pt_energy from per-triplet contributions:
@@ -849,16 +980,66 @@ __global__ void neumaier_sum(const double* __restrict__ e, int64_t n, double* ou
 
 size_t energy_smem_bytes(bool f64) { return 3 * TB * TB * TP * (f64 ? 8 : 4); }
 
-// float32-X path: V-table prep + energy (grid: nchunks x ntrip).
+// Dynamic shared memory of the TMA-staged variant: two stages of three
+// sub-cubes, two mbarriers, 1024 bytes of alignment slack.
+constexpr int kRingBytes = 6 * TB * TB * TB * 4 + 16 + 1024;
+
+// Resident CTAs per SM of one energy_f32 variant (queried once).
+template <bool M, bool F, bool U, bool L, bool T>
+int ef32_resident() {
+  static int occ = 0;
+  if (occ == 0) {
+    int n = 0;
+    auto k = energy_f32<M, F, U, L, T>;
+    if (T) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256, T ? kRingBytes : 0) !=
+        cudaSuccess)
+      n = 1;
+    occ = n > 0 ? n : 1;
+  }
+  return occ;
+}
+
+template <bool M, bool F, bool U, bool L, bool T>
+void launch_ef32(EnergyArgs a, const float* X, const float* Z, const float* vtab,
+                 int64_t vt_stride, int pv, int pvt, int64_t vt_half, int ntrip, int nchunks,
+                 const CUtensorMap& mx, const CUtensorMap& mz, cudaStream_t st) {
+  a.nchunk = nchunks;
+  a.nitems = ntrip * nchunks;
+  const int grid = std::max(1, std::min(a.nitems, ef32_resident<M, F, U, L, T>() * a.nsm));
+  energy_f32<M, F, U, L, T><<<grid, 256, T ? kRingBytes : 0, st>>>(a, X, Z, vtab, vt_stride, pv,
+                                                                   pvt, vt_half, mx, mz);
+}
+
+// Tensor maps of the TMA-staged mixed variant over one group's Y (rows b nvt
+// + C, pitch pitch_x) and Z' (rows pair(a, b), pitch pitch_z).
+int cube_maps(const EnergyArgs& a, const float* X, const float* Z, int ntrip, CUtensorMap* mx,
+              CUtensorMap* mz) {
+  const int64_t dx[4] = {a.pitch_x, a.nvt, a.nvs, ntrip};
+  const int64_t sx[3] = {(int64_t)a.pitch_x * 4, (int64_t)a.nvt * a.pitch_x * 4, a.x_stride * 4};
+  const int bx[4] = {TB, TB, TB, 1};
+  const int64_t nrow = a.pitch_z > 0 ? a.z_stride / a.pitch_z : 0;
+  const int64_t dz[3] = {a.pitch_z, std::max<int64_t>(nrow, 1), ntrip};
+  const int64_t sz[2] = {(int64_t)a.pitch_z * 4, a.z_stride * 4};
+  const int bz[3] = {TB, TB, 1};
+  int rc = make_f32_map(mx, X, 4, dx, sx, bx, true);
+  if (rc == LNO_OT_OK) rc = make_f32_map(mz, Z, 3, dz, sz, bz, false);
+  return rc;
+}
+
+// float32-X path: V-table prep + energy (nchunks items per triplet on a
+// persistent grid; partial holds 8 values per item).
 cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* Z, float* vtab,
                               int64_t vt_stride, int pv, int pvt, int ntrip, int nchunks,
                               cudaStream_t st) {
   if (ntrip <= 0) return cudaSuccess;
+  if (nchunks < 1 || nchunks > a.nblocks || a.nsm < 1) return cudaErrorInvalidValue;
   dim3 gp(64, ntrip);
   energy_prep<<<gp, 256, 0, st>>>(a, vtab, vt_stride, pv, pvt);
-  dim3 grid(nchunks, ntrip);
+  static const CUtensorMap none{};
 #define LNO_EF32(M, F, L) \
-  energy_f32<M, F, false, L><<<grid, 256, 0, st>>>(a, X, Z, vtab, vt_stride, pv, pvt, 0)
+  launch_ef32<M, F, false, L, false>(a, X, Z, vtab, vt_stride, pv, pvt, 0, ntrip, nchunks, none, \
+                                     none, st)
   const bool lap = a.lap_w != 0.0;
   if (a.kind == SAME) {
     if (a.vmode) {
@@ -866,12 +1047,19 @@ cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* 
     } else {
       if (lap) LNO_EF32(false, false, true); else LNO_EF32(false, false, false);
     }
+  } else if (a.vmode) {
+    if (lap) LNO_EF32(true, true, true); else LNO_EF32(true, true, false);
   } else {
-    if (a.vmode) {
-      if (lap) LNO_EF32(true, true, true); else LNO_EF32(true, true, false);
-    } else {
-      if (lap) LNO_EF32(true, false, true); else LNO_EF32(true, false, false);
-    }
+    // mixed spin: sub-cubes staged by TMA
+    if (a.flag == nullptr || a.pitch_x % 16 || a.pitch_z % 16) return cudaErrorInvalidValue;
+    CUtensorMap mx, mz;
+    if (cube_maps(a, X, Z, ntrip, &mx, &mz) != LNO_OT_OK) return cudaErrorInvalidValue;
+    if (lap)
+      launch_ef32<true, false, false, true, true>(a, X, Z, vtab, vt_stride, pv, pvt, 0, ntrip,
+                                                  nchunks, mx, mz, st);
+    else
+      launch_ef32<true, false, false, false, true>(a, X, Z, vtab, vt_stride, pv, pvt, 0, ntrip,
+                                                   nchunks, mx, mz, st);
   }
 #undef LNO_EF32
   return cudaGetLastError();
@@ -895,19 +1083,20 @@ cudaError_t launch_energy_f32_fused(const EnergyArgs& a, const float* X, const f
                                    int nchunks, cudaStream_t st) {
   if (ntrip <= 0) return cudaSuccess;
   if (a.kind == SAME) return cudaErrorInvalidValue;
+  if (nchunks < 1 || nchunks > a.nblocks || a.nsm < 1) return cudaErrorInvalidValue;
   dim3 gp(64, ntrip);
   EnergyArgs a0 = a, a1 = a;
   a0.vmode = 0;
   a1.vmode = 1;
   energy_prep<<<gp, 256, 0, st>>>(a0, vtab, 2 * vt_half, pv, pvt);
   energy_prep<<<gp, 256, 0, st>>>(a1, vtab + vt_half, 2 * vt_half, pv, pvt);
-  dim3 grid(nchunks, ntrip);
+  static const CUtensorMap none{};
   if (a.lap_w != 0.0)
-    energy_f32<true, false, true, true><<<grid, 256, 0, st>>>(a0, X, Z, vtab, 2 * vt_half, pv,
-                                                             pvt, vt_half);
+    launch_ef32<true, false, true, true, false>(a0, X, Z, vtab, 2 * vt_half, pv, pvt, vt_half,
+                                                ntrip, nchunks, none, none, st);
   else
-    energy_f32<true, false, true, false><<<grid, 256, 0, st>>>(a0, X, Z, vtab, 2 * vt_half, pv,
-                                                              pvt, vt_half);
+    launch_ef32<true, false, true, false, false>(a0, X, Z, vtab, 2 * vt_half, pv, pvt, vt_half,
+                                                 ntrip, nchunks, none, none, st);
   return cudaGetLastError();
 }
 
@@ -932,7 +1121,7 @@ cudaError_t launch_energy(const EnergyArgs& a, const void* X, const void* Z, boo
 cudaError_t launch_reduce_partials(const double* partial, int np, const double* partial2,
                                    int ntrip, double* e_trip, cudaStream_t st) {
   if (ntrip <= 0) return cudaSuccess;
-  reduce_partials<<<ceil_div(ntrip, 128), 128, 0, st>>>(partial, np, partial2, ntrip, e_trip);
+  reduce_partials<<<ceil_div(ntrip, 8), 256, 0, st>>>(partial, np, partial2, ntrip, e_trip);
   return cudaGetLastError();
 }
 

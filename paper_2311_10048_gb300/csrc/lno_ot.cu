@@ -68,6 +68,12 @@ cudaError_t launch_pack_at2(const int2*, int, int, int, int, int, int, int, cons
                             const double*, St, cudaStream_t);
 cudaError_t launch_transpose_t2ab(const double*, int, int, int, int, double*, cudaStream_t);
 cudaError_t launch_absmax(const double*, int64_t, unsigned long long*, cudaStream_t);
+cudaError_t launch_view_absmax(const double* in, int64_t rs, int64_t ks, int rows, int K,
+                               unsigned long long* out, cudaStream_t s);
+template <int S>
+cudaError_t launch_view_slices(const double* in, int64_t rs, int64_t ks, int rows, int K,
+                               int Kp, __nv_bfloat16* out, int64_t slice_stride, double inv,
+                               cudaStream_t s);
 cudaError_t launch_t2ab_flip_mismatch(const double* t2ab, int n, int v, double tol,
                                      unsigned int* count, cudaStream_t s);
 cudaError_t launch_gather_rows(const void* src, void* dst, const int* list, int nlist,
@@ -261,23 +267,31 @@ const CUtensorMap& map_for(const Operand& op, int box) {
   return box == 256 ? op.map256 : box == 96 ? op.map96 : box == 64 ? op.map64 : op.map128;
 }
 
-// One grouped W-contraction launch with float32 output.
+// One grouped W-contraction launch with float32 output XT[n][m] (pitch ldo)
+// = sum_seg A_seg[m] . B_seg[n], m < M the virtual index of the A operands, n
+// < N the (pair) rows of the B operands.  The kernel runs it row-major with
+// the roles exchanged: its 128-row tiles run over the N rows (a long
+// dimension, so they are full) and its n-tiles over the M rows, the last one
+// only as wide as needed (M rounded up to 16).  seg_tc stores the segments
+// with the roles already exchanged.
 cudaError_t launch_contract(int S, bool tf, int bn_req, const Operand& A0, const Operand& A1,
                             const Operand& B0, const Operand& B1, const TcProb* dpt, int nprob,
                             int M, int N, int ldo, double scale, int* flag, int nsm,
                             cudaStream_t st) {
   const int bn = contract_bn(S, bn_req);
-  CUtensorMap mA[2] = {A0.map128, A1.map128};
-  CUtensorMap mB[2] = {map_for(B0, bn), map_for(B1, bn)};
+  CUtensorMap mA[2] = {B0.map128, B1.map128};
+  CUtensorMap mB[2] = {map_for(A0, bn), map_for(A1, bn)};
   const TcDiag dg = tc_normal();
-#define LNO_CALL(SS, BB) \
-  launch_tc_gemm<SS, BB, float>(mA, mB, dpt, nprob, M, N, ldo, scale, flag, nullptr, nsm, st, dg)
+  std::swap(M, N);
+#define LNO_CALL(SS, BB)                                                                      \
+  launch_tc_gemm<SS, BB, float, false, true>(mA, mB, dpt, nprob, M, N, ldo, scale, flag, nullptr, \
+                                             nsm, st, dg)
   if (tf)
     return bn == 128
-               ? launch_tc_gemm<2, 128, float, true>(mA, mB, dpt, nprob, M, N, ldo, scale, flag,
-                                                     nullptr, nsm, st, dg)
-               : launch_tc_gemm<2, 256, float, true>(mA, mB, dpt, nprob, M, N, ldo, scale, flag,
-                                                     nullptr, nsm, st, dg);
+               ? launch_tc_gemm<2, 128, float, true, true>(mA, mB, dpt, nprob, M, N, ldo, scale,
+                                                           flag, nullptr, nsm, st, dg)
+               : launch_tc_gemm<2, 256, float, true, true>(mA, mB, dpt, nprob, M, N, ldo, scale,
+                                                           flag, nullptr, nsm, st, dg);
   if (S == 2) return bn == 128 ? LNO_CALL(2, 128) : LNO_CALL(2, 256);
   if (S == 3) return bn == 64 ? LNO_CALL(3, 64) : LNO_CALL(3, 128);
   if (S == 4) return bn == 64 ? LNO_CALL(4, 64) : bn == 96 ? LNO_CALL(4, 96) : LNO_CALL(4, 128);
@@ -292,6 +306,7 @@ struct Run {
   Arena arena;
   bool f64;
   bool tf32 = false;  // W contraction operands as TF32 slices (precision TF32)
+  bool tc_adjoint = false;  // adjoint: its contractions on the tensor cores (tc_matmul)
   int S = 0;          // slices of the W contraction operands
   int Sdf = 4;        // slices of the DF factors
   double sigT = 1, sigI = 1, sigB = 1;
@@ -861,9 +876,11 @@ struct SpinPass {
                double sign) {
     sg = SegF64{A.f64 + arow * A.Kp, B.f64 + brow * B.Kp, A.K, A.Kp, B.Kp, sign};
   }
+  // roles exchanged for the row-major launch (launch_contract): the kernel's
+  // A is the pair operand B, its B the virtual operand A
   void seg_tc(TcSeg& sg, int amap, const Operand& A, int64_t arow, int bmap, const Operand& B,
               int64_t brow, int neg) {
-    sg = TcSeg{amap, bmap, (int)arow, (int)brow, A.K, neg};
+    sg = TcSeg{bmap, amap, (int)brow, (int)arow, A.K, neg};
   }
 
   int run_case(bool is_mixed) {
@@ -924,11 +941,17 @@ struct SpinPass {
     TRY(A.get(&dtrips, (size_t)ntrip));
     CU(cudaMemcpyAsync(dtrips, cs.trips.data(), ntrip * sizeof(Trip), cudaMemcpyHostToDevice,
                        R.st));
-    const int target = R.ctx->nsm * 6;
-    const int P = std::max(1, std::min((int)blocks.size(), target / Gshape + 1));
+    // float64 path: P chunks per triplet, one CTA each.  Float32 path: P
+    // items per triplet on a persistent grid, about 32 items per resident CTA
+    // in a full group (so the last round of items is a small fraction), one
+    // partial per warp and item.
+    const int P = f64 ? std::max(1, std::min((int)blocks.size(), R.ctx->nsm * 6 / Gshape + 1))
+                      : std::max(1, std::min((int)blocks.size(),
+                                             (64 * R.ctx->nsm + Gshape - 1) / Gshape));
+    const int npart = f64 ? P : 8 * P;   // partials per triplet
     const bool fov = R.fov[0] != nullptr;   // restricted open-shell f_ov term
     double* partial;
-    TRY(A.get(&partial, (size_t)G * P * (fov ? 2 : 1)));
+    TRY(A.get(&partial, (size_t)G * npart * (fov ? 2 : 1)));
     // float32 V tables of the tensor-core path, per triplet
     const int pv = (int)round_up(std::max(v, 1), 16), pvt = (int)round_up(std::max(vt, 1), 16);
     const int64_t vt_stride = is_mixed ? round_up(2LL * v * pvt + (int64_t)v * pv, 16)
@@ -968,6 +991,8 @@ struct SpinPass {
     ea.z_stride = N2 * P2;
     ea.lap_s = R.lap_s;
     ea.lap_w = R.lap_w;
+    ea.nsm = R.ctx->nsm;
+    ea.flag = R.ctx->d_flag;
 
     // stats
     const double dv = v, dvt = vt;
@@ -1099,7 +1124,7 @@ struct SpinPass {
         ef.t1t = R.fov[is_mixed ? t : s];
         ef.t2ss = t2ss;
         ef.t2st = t2st;
-        ef.partial = partial2 = partial + (size_t)G * P;
+        ef.partial = partial2 = partial + (size_t)G * npart;
         if (f64)
           CU(launch_energy(ef, X, Z, f64, ng, P, R.st));
         else
@@ -1108,7 +1133,7 @@ struct SpinPass {
                                P, R.st));
         R.stats->energy_launches += 2;
       }
-      CU(launch_reduce_partials(partial, P, partial2, ng, eout + g0, R.st));
+      CU(launch_reduce_partials(partial, npart, partial2, ng, eout + g0, R.st));
       if (e1) cudaEventRecord(e1, R.st);
       if (e0 && e1) R.energy_ev.push_back({e0, e1});
       R.stats->energy_launches += 2;
@@ -1719,12 +1744,90 @@ int zero_operand_like(Arena& A, const Operand& src, Operand& d, cudaStream_t st)
   return zeros(A, &d.f64, n, st);
 }
 
+// Strided float64 view: element (r, k) at p[r rs + k ks].
+struct View {
+  const double* p;
+  int64_t rs, ks;
+};
+
+// C[m ldc + n] (+)= alpha sum_k a(m, k) b(n, k) on the tensor cores: both views
+// are cut into 4 exact BF16 slices with power-of-two scales (the DF assembly's
+// representation, 10 slice products, float64 output of the exact class sums).
+// Used by the adjoint of the tensor-core precisions.
+int tc_matmul(Run& R, Arena& A, int M, int N, int K, View a, View b, double* C, int64_t ldc,
+              double alpha, bool accum) {
+  if (M <= 0 || N <= 0 || K <= 0) return LNO_OT_OK;
+  constexpr int S = 4;
+  cudaStream_t st = R.st;
+  unsigned long long* am = R.ctx->d_amax;
+  CU(cudaMemsetAsync(am, 0, 2 * sizeof(unsigned long long), st));
+  CU(launch_view_absmax(a.p, a.rs, a.ks, M, K, am, st));
+  CU(launch_view_absmax(b.p, b.rs, b.ks, N, K, am + 1, st));
+  unsigned long long hb[2];
+  CU(cudaMemcpyAsync(hb, am, sizeof hb, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  double amax[2];
+  std::memcpy(amax, hb, sizeof amax);
+  if (!std::isfinite(amax[0]) || !std::isfinite(amax[1])) return LNO_OT_EINVAL;
+  if (amax[0] == 0.0 || amax[1] == 0.0) {   // a zero operand: nothing to add
+    if (!accum)
+      for (int m = 0; m < M; ++m)
+        CU(cudaMemsetAsync(C + (int64_t)m * ldc, 0, (size_t)N * sizeof(double), st));
+    return LNO_OT_OK;
+  }
+  auto pow2_at_least = [](double x) {
+    int e;
+    const double f = std::frexp(x, &e);
+    return std::ldexp(1.0, f == 0.5 ? e - 1 : e);
+  };
+  const double sa = pow2_at_least(amax[0]), sb = pow2_at_least(amax[1]);
+  const int64_t Kp = round_up(K, 8);
+  __nv_bfloat16 *qa, *qb;
+  TRY(A.get(&qa, (size_t)(S * M * Kp)));
+  TRY(A.get(&qb, (size_t)(S * N * Kp)));
+  CU(launch_view_slices<S>(a.p, a.rs, a.ks, M, K, (int)Kp, qa, (int64_t)M * Kp, 128.0 / sa, st));
+  CU(launch_view_slices<S>(b.p, b.rs, b.ks, N, K, (int)Kp, qb, (int64_t)N * Kp, 128.0 / sb, st));
+  // the kernel writes its output transposed: its rows (A role) are n, its
+  // columns (B role) m, so out[m ldc + n]
+  CUtensorMap mA[2], mB[2];
+  TRY(make_operand_map(&mA[0], qb, Kp, N, S, (int64_t)N * Kp, 128));
+  TRY(make_operand_map(&mB[0], qa, Kp, M, S, (int64_t)M * Kp, 128));
+  mA[1] = mA[0];
+  mB[1] = mB[0];
+  TcProb p{};
+  p.nseg = 1;
+  p.seg[0] = TcSeg{0, 0, 0, 0, K, alpha < 0 ? 1 : 0};
+  p.accum = accum ? 1 : 0;
+  p.out = C;
+  TcProb* dp;
+  TRY(A.get(&dp, 1));
+  CU(cudaMemcpyAsync(dp, &p, sizeof p, cudaMemcpyHostToDevice, st));
+  const double scale = sa * sb * std::ldexp(1.0, -14) * std::fabs(alpha);
+  CU((launch_tc_gemm<4, 128, double, false, false>(mA, mB, dp, 1, N, M, (int)ldc, scale,
+                                                   R.ctx->d_flag, nullptr, R.ctx->nsm, st,
+                                                   tc_normal())));
+  R.stats->contract_launches++;
+  R.stats->other_launches += 4;
+  A.drop(qa);
+  A.drop(qb);
+  A.drop(dp);
+  return LNO_OT_OK;
+}
+
 // DF adjoint: out[n][m] = sum_Q L[l0+m][Q] R[r0+n][Q]  ->  dL, dR (+=)
 int df_adjoint(Run& R, Arena& A, const Operand& Lo, Operand& dL, int64_t l0, int M,
                const Operand& Ro, Operand& dR, int64_t r0, int N, const double* dout, int ldo) {
   if (M <= 0 || N <= 0) return LNO_OT_OK;
-  GemmS g[2];
   const int64_t Qp = Lo.Kp;
+  if (R.tc_adjoint) {
+    // dL[l0+m][Q] += sum_n dout[n][m] R[r0+n][Q];  dR[r0+n][Q] += sum_m dout[n][m] L[l0+m][Q]
+    TRY(tc_matmul(R, A, M, R.naux, N, View{dout, 1, ldo}, View{Ro.f64 + r0 * Qp, 1, Qp},
+                  dL.f64 + l0 * Qp, Qp, 1.0, true));
+    TRY(tc_matmul(R, A, N, R.naux, M, View{dout, ldo, 1}, View{Lo.f64 + l0 * Qp, 1, Qp},
+                  dR.f64 + r0 * Qp, Qp, 1.0, true));
+    return LNO_OT_OK;
+  }
+  GemmS g[2];
   g[0] = GemmS{dout, Ro.f64 + r0 * Qp, dL.f64 + l0 * Qp, M, R.naux, N, 0,
                1, ldo, Qp, 1, Qp, 1, 1.0};
   g[1] = GemmS{dout, Lo.f64 + l0 * Qp, dR.f64 + r0 * Qp, N, R.naux, M, 0,
@@ -1869,11 +1972,30 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
         if (is_mixed) fill(pf2[g], segs2[g], Z + (size_t)g * N2 * P2);
       }
       // recompute X (and Z')
-      CU(cudaMemcpyAsync(dpf, pf.data(), ng * sizeof(ProbF64), cudaMemcpyHostToDevice, st));
-      CU(launch_gemm_f64(dpf, ng, M1, (int)N1, P1, st));
-      if (is_mixed) {
-        CU(cudaMemcpyAsync(dpf2, pf2.data(), ng * sizeof(ProbF64), cudaMemcpyHostToDevice, st));
-        CU(launch_gemm_f64(dpf2, ng, M2, (int)N2, P2, st));
+      if (R.tc_adjoint) {
+        // XT[n][m] = sum_seg sign A[arow+m][:] . B[brow+n][:], one tensor-core
+        // product per segment, the later ones added
+        auto recompute = [&](const std::vector<std::vector<SegRef>>& segs, double* Xb, int64_t Nn,
+                             int Mm, int ldo) -> int {
+          for (int g = 0; g < ng; ++g)
+            for (size_t q = 0; q < segs[g].size(); ++q) {
+              const SegRef& r = segs[g][q];
+              TRY(tc_matmul(R, A, (int)Nn, Mm, r.A->K,
+                            View{r.B->f64 + r.brow * r.B->Kp, r.B->Kp, 1},
+                            View{r.A->f64 + r.arow * r.A->Kp, r.A->Kp, 1},
+                            Xb + (size_t)g * Nn * ldo, ldo, r.sign, q > 0));
+            }
+          return LNO_OT_OK;
+        };
+        TRY(recompute(segs1, X, N1, M1, P1));
+        if (is_mixed) TRY(recompute(segs2, Z, N2, M2, P2));
+      } else {
+        CU(cudaMemcpyAsync(dpf, pf.data(), ng * sizeof(ProbF64), cudaMemcpyHostToDevice, st));
+        CU(launch_gemm_f64(dpf, ng, M1, (int)N1, P1, st));
+        if (is_mixed) {
+          CU(cudaMemcpyAsync(dpf2, pf2.data(), ng * sizeof(ProbF64), cudaMemcpyHostToDevice, st));
+          CU(launch_gemm_f64(dpf2, ng, M2, (int)N2, P2, st));
+        }
       }
       // energy adjoint -> dX, dT1, deps, V-integral gradients
       CU(cudaMemsetAsync(dX, 0, (size_t)ng * N1 * P1 * sizeof(double), st));
@@ -1895,6 +2017,22 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
       // contraction adjoint: dA += sign dX.B, dB += sign dX^T.A
       auto adj = [&](const std::vector<std::vector<SegRef>>& segs, const double* dXb, int64_t Nn,
                      int Mm, int ldo) -> int {
+        if (R.tc_adjoint) {
+          // dA[arow+m][k] += s sum_n dX[n][m] B[brow+n][k]
+          // dB[brow+n][k] += s sum_m dX[n][m] A[arow+m][k]
+          for (int g = 0; g < ng; ++g)
+            for (const SegRef& r : segs[g]) {
+              const double* dxg = dXb + (size_t)g * Nn * ldo;
+              const int K = r.A->K;
+              TRY(tc_matmul(R, A, Mm, K, (int)Nn, View{dxg, 1, ldo},
+                            View{r.B->f64 + r.brow * r.B->Kp, 1, r.B->Kp},
+                            r.dA->f64 + r.arow * r.A->Kp, r.A->Kp, r.sign, true));
+              TRY(tc_matmul(R, A, (int)Nn, K, Mm, View{dxg, ldo, 1},
+                            View{r.A->f64 + r.arow * r.A->Kp, 1, r.A->Kp},
+                            r.dB->f64 + r.brow * r.B->Kp, r.B->Kp, r.sign, true));
+            }
+          return LNO_OT_OK;
+        }
         for (int q = 0; q < 3; ++q) {  // one launch per segment position
           std::vector<GemmS> ga, gb;
           int maxKa = 0;
@@ -2048,6 +2186,10 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
   Run R(ctx, dom);
   R.f64 = true;
   R.S = 0;
+  // float64 operands and energy adjoint; with a tensor-core precision the
+  // contractions (X recompute, contraction and DF adjoints) run on the tensor
+  // cores through tc_matmul
+  R.tc_adjoint = ctx->prec != LNO_OT_FP64;
   CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
   CaseSel cs[4];
   for (int c = 0; c < 4; ++c) TRY(select_case(dom, c, cs[c]));

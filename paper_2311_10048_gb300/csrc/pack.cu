@@ -27,6 +27,8 @@
 // BF16 slices of the tensor-core path (value = scale 2^-7 (s1 + s2 + s3),
 // s1 an integer in [-128, 128], s2 a multiple of 2^-8 in [-1/2, 1/2], ...,
 // each step rounded to nearest).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace lno {
@@ -228,6 +230,57 @@ __global__ void transpose_t2ab(const double* __restrict__ t2ab, int na, int nb, 
   }
 }
 
+// Strided float64 views for the tensor-core adjoint: element (r, k) of a
+// rows x K view sits at in[r rs + k ks].  Work goes in 32 x 32 tiles whose
+// loads run along the view's unit-stride index (k when ks == 1, else r), so
+// they coalesce either way.
+__device__ __forceinline__ double view_at(const double* in, int64_t rs, int64_t ks, int rows,
+                                          int K, int r, int k) {
+  return (r < rows && k < K) ? in[(int64_t)r * rs + (int64_t)k * ks] : 0.0;
+}
+
+// max |x| over the view (bits of a non-negative double, atomicMax into *out)
+__global__ void view_absmax(const double* __restrict__ in, int64_t rs, int64_t ks, int rows,
+                            int K, unsigned long long* __restrict__ out) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool rfast = ks != 1 && rs == 1;
+  double m = 0.0;
+  for (int r0 = blockIdx.y * 32; r0 < rows; r0 += gridDim.y * 32) {
+    const int k0 = blockIdx.x * 32;
+    for (int i = ty; i < 32; i += 8) {
+      const double x = rfast ? view_at(in, rs, ks, rows, K, r0 + tx, k0 + i)
+                             : view_at(in, rs, ks, rows, K, r0 + i, k0 + tx);
+      m = fmax(m, fabs(x));
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  if ((tx & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// view -> S BF16 slices [s][r][Kp] (k-contiguous rows, zero for k >= K)
+template <int S>
+__global__ void view_slices(const double* __restrict__ in, int64_t rs, int64_t ks, int rows,
+                            int K, int Kp, StoreSlices<S> st) {
+  __shared__ double t[32][33];   // [k][r]
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool rfast = ks != 1 && rs == 1;
+  const int k0 = blockIdx.x * 32;
+  for (int r0 = blockIdx.y * 32; r0 < rows; r0 += gridDim.y * 32) {
+    for (int i = ty; i < 32; i += 8) {
+      if (rfast)
+        t[i][tx] = view_at(in, rs, ks, rows, K, r0 + tx, k0 + i);
+      else
+        t[tx][i] = view_at(in, rs, ks, rows, K, r0 + i, k0 + tx);
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int r = r0 + i, k = k0 + tx;
+      if (r < rows && k < Kp) st((int64_t)r * Kp + k, t[tx][i], 1);
+    }
+    __syncthreads();
+  }
+}
+
 // max |x| over n doubles, as the bits of a non-negative double in *out (atomicMax).
 __global__ void absmax_kernel(const double* __restrict__ x, int64_t n,
                               unsigned long long* __restrict__ out) {
@@ -403,6 +456,29 @@ cudaError_t launch_absmax(const double* x, int64_t n, unsigned long long* out, c
   absmax_kernel<<<grid_for(n), 256, 0, s>>>(x, n, out);
   return cudaGetLastError();
 }
+
+cudaError_t launch_view_absmax(const double* in, int64_t rs, int64_t ks, int rows, int K,
+                               unsigned long long* out, cudaStream_t s) {
+  if (rows <= 0 || K <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((K + 31) / 32), (unsigned)std::min((rows + 31) / 32, 4096));
+  view_absmax<<<grid, dim3(32, 8), 0, s>>>(in, rs, ks, rows, K, out);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_view_slices(const double* in, int64_t rs, int64_t ks, int rows, int K,
+                               int Kp, __nv_bfloat16* out, int64_t slice_stride, double inv,
+                               cudaStream_t s) {
+  if (rows <= 0 || Kp <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)std::min((rows + 31) / 32, 4096));
+  view_slices<S><<<grid, dim3(32, 8), 0, s>>>(in, rs, ks, rows, K, Kp,
+                                               StoreSlices<S>{out, slice_stride, inv, inv});
+  return cudaGetLastError();
+}
+template cudaError_t launch_view_slices<4>(const double*, int64_t, int64_t, int, int, int,
+                                           __nv_bfloat16*, int64_t, double, cudaStream_t);
+template cudaError_t launch_view_slices<5>(const double*, int64_t, int64_t, int, int, int,
+                                           __nv_bfloat16*, int64_t, double, cudaStream_t);
 
 #define LNO_INST(St)                                                                           \
   template cudaError_t launch_transpose_block<St>(const double*, int, int, int, int, int, int,  \

@@ -42,6 +42,7 @@
 // Every mbarrier wait is bounded; on a timeout the kernel records an error
 // code, drains its own TMA copies and MMAs, frees TMEM and returns.
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace lno {
 
@@ -51,32 +52,6 @@ constexpr int BM = 128;
 constexpr int BK = 32;                     // BF16 elements per 64-byte row, SWIZZLE_64B
 constexpr long long kWaitCycles = 4000000000LL;
 constexpr int kSmemBudget = 227 * 1024;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 
 // Wait for phase `parity` of `bar`; false if another role raised the error
 // flag (abortable) or `limit` cycles passed (then records `code`).  Waits for
@@ -96,15 +71,6 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* flag,
       }
     }
   }
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                            int c0, int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -132,6 +98,44 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint6
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
+}
+
+// The same MMAs with a collector-buffer usage for A: consecutive MMAs that
+// share one A operand (slice pa against the slices pb of B) read it from shared
+// memory once (fill), then from the collector (use, lastuse).
+#define LNO_UMMA_C(NAME, KIND, COLL)                                                        \
+  __device__ __forceinline__ void NAME(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,     \
+                                       uint32_t idesc, uint32_t accum) {                    \
+    asm volatile("{\n\t.reg .pred p;\n\t"                                                   \
+                 "setp.ne.b32 p, %4, 0;\n\t"                                               \
+                 "tcgen05.mma.cta_group::1.kind::" KIND ".collector::a::" COLL                \
+                 " [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),                                 \
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)                             \
+                 : "memory");                                                               \
+  }
+LNO_UMMA_C(umma_bf16_fill, "f16", "fill")
+LNO_UMMA_C(umma_bf16_use, "f16", "use")
+LNO_UMMA_C(umma_bf16_last, "f16", "lastuse")
+LNO_UMMA_C(umma_tf32_fill, "tf32", "fill")
+LNO_UMMA_C(umma_tf32_use, "tf32", "use")
+LNO_UMMA_C(umma_tf32_last, "tf32", "lastuse")
+#undef LNO_UMMA_C
+
+// mode 0: no collector, 1: fill, 2: use, 3: last use
+template <bool TF>
+__device__ __forceinline__ void umma_any(int mode, uint32_t d, uint64_t a, uint64_t b,
+                                         uint32_t id, uint32_t acc) {
+  if constexpr (TF) {
+    if (mode == 1) umma_tf32_fill(d, a, b, id, acc);
+    else if (mode == 2) umma_tf32_use(d, a, b, id, acc);
+    else if (mode == 3) umma_tf32_last(d, a, b, id, acc);
+    else umma_tf32(d, a, b, id, acc);
+  } else {
+    if (mode == 1) umma_bf16_fill(d, a, b, id, acc);
+    else if (mode == 2) umma_bf16_use(d, a, b, id, acc);
+    else if (mode == 3) umma_bf16_last(d, a, b, id, acc);
+    else umma_bf16(d, a, b, id, acc);
+  }
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -176,12 +180,28 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
 }
 
 // Instruction descriptor: D FP32, A/B K-major of format 1 (BF16, kind::f16)
-// or 2 (TF32, kind::tf32), M=128, N=BN.
-template <int BN, bool TF>
-__device__ __forceinline__ uint32_t idesc_mma(int neg) {
+// or 2 (TF32, kind::tf32), M=128, N=n (a multiple of 16, 16..256).
+template <bool TF>
+__device__ __forceinline__ uint32_t idesc_mma(int neg, int n) {
   constexpr uint32_t fmt = TF ? 2u : 1u;
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)neg << 13) |
-         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+// 16 consecutive floats of one output row; `left` columns remain in the row
+// (the rest of the 16 are not written).  16-byte aligned when left >= 16.
+__device__ __forceinline__ void store_row16(float* p, const uint32_t (&v)[16], int left) {
+  if (left >= 16) {
+    float4* p4 = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      p4[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                          __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < left) p[j] = __uint_as_float(v[j]);
+  }
 }
 
 template <int S, int BN>
@@ -204,7 +224,10 @@ struct Cfg {
 // TF: TF32 slices (32-bit elements, 16 per 64-byte row, K 8 per MMA) instead
 // of BF16 ones (32 per row, K 16 per MMA); the shared-memory layout, the
 // descriptors and the MMAs per row are the same in bytes.
-template <int S, int BN, typename OutT, bool TF>
+// RM: row-major output out[m][n] (pitch ldo), n-tiles fastest; otherwise the
+// transposed out[n][m], m-tiles fastest.  The last n-tile's MMAs are only as
+// wide as its columns (rounded up to 16), so a narrow n costs little.
+template <int S, int BN, typename OutT, bool TF, bool RM>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
@@ -233,13 +256,24 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
   auto b_addr = [&](int st, int sl) {
     return smem_u32(smem + st * C::kStage + S * C::kABytes + sl * C::kBBytes);
   };
-  // unit -> (problem, m-tile, n-tile), m fastest
+  // unit -> (problem, m-tile, n-tile): m fastest (transposed output: the
+  // concurrent CTAs share one n-tile of B), n fastest for RM (they share one
+  // m-tile of A)
   auto decode = [&](long long u, int& mt, int& nt, long long& pr) {
-    mt = (int)(u % nM);
-    const long long r = u / nM;
-    nt = (int)(r % nN);
-    pr = r / nN;
+    if constexpr (RM) {
+      nt = (int)(u % nN);
+      const long long r = u / nN;
+      mt = (int)(r % nM);
+      pr = r / nM;
+    } else {
+      mt = (int)(u % nM);
+      const long long r = u / nM;
+      nt = (int)(r % nN);
+      pr = r / nN;
+    }
   };
+  // MMA width of n-tile nt: its columns rounded up to 16
+  auto ntile_w = [&](int nt) { return min(BN, (N - nt * BN + 15) & ~15); };
 
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -249,7 +283,7 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     mbar_init(tfull, 1);
     mbar_init(tempty, 128);
     mbar_init(drain, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -321,9 +355,10 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
         }
         tc_fence_after();
         uint32_t cls_on = 0;  // bit g: accumulator of class g already written
+        const int nw = ntile_w(nt);
         for (int sg = 0; sg < P.nseg && ok; ++sg) {
           const TcSeg seg = P.seg[sg];
-          const uint32_t idesc = idesc_mma<BN, TF>(seg.neg);
+          const uint32_t idesc = idesc_mma<TF>(seg.neg, nw);
           for (int k0 = 0; k0 < seg.K; k0 += BKE) {
             if (!mbar_wait(full_bar(stage), phase, flag, 3, true, wlim)) {
               ok = false;
@@ -335,15 +370,15 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
               if (k0 + ks * KM < seg.K) {
 #pragma unroll
                 for (int pa = 0; pa < S; ++pa) {
+                  const uint64_t ad = sdesc_sw64(a_addr(stage, pa) + ks * 32);
 #pragma unroll
                   for (int pb = 0; pb + pa < S; ++pb) {
-                    const uint64_t ad = sdesc_sw64(a_addr(stage, pa) + ks * 32);
                     const uint64_t bd = sdesc_sw64(b_addr(stage, pb) + ks * 32);
                     const int g = pa + pb;
-                    if constexpr (TF)
-                      umma_tf32(tmem + g * BN, ad, bd, idesc, (cls_on >> g) & 1u);
-                    else
-                      umma_bf16(tmem + g * BN, ad, bd, idesc, (cls_on >> g) & 1u);
+                    // A slice pa meets S - pa slices of B in a row: read it once
+                    const int last = S - 1 - pa;
+                    const int mode = last == 0 ? 0 : pb == 0 ? 1 : pb == last ? 3 : 2;
+                    umma_any<TF>(mode, tmem + g * BN, ad, bd, idesc, (cls_on >> g) & 1u);
                     cls_on |= 1u << g;
                     any = true;
                   }
@@ -387,8 +422,9 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
         // combine the classes into the spare TMEM columns, free the class
         // accumulators for the next tile's MMAs, then store from the spare copy
         const uint32_t spare = tbase + S * BN;
+        const int nch = ntile_w(nt) / 16;
 #pragma unroll 1
-        for (int c = 0; c < BN / 16; ++c) {
+        for (int c = 0; c < nch; ++c) {
           uint32_t acc[S][16];
 #pragma unroll
           for (int g = 0; g < S; ++g) tmem_ld16(tbase + g * BN + c * 16, acc[g]);
@@ -407,27 +443,45 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
         tc_fence_before();
         mbar_arrive(tempty);
 #pragma unroll 1
-        for (int c = 0; c < BN / 16; ++c) {
+        for (int c = 0; c < nch; ++c) {
           uint32_t v[16];
           tmem_ld16(spare + c * 16, v);
           tmem_ld_wait();
           const int n0 = nt * BN + c * 16;
-          OutT* op = out + (int64_t)n0 * ldo + m;
+          if constexpr (RM) {
+            if (mok) store_row16(reinterpret_cast<float*>(out) + (int64_t)m * ldo + n0, v, N - n0);
+          } else {
+            OutT* op = out + (int64_t)n0 * ldo + m;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float x = __uint_as_float(v[j]);
-            if (mok && n0 + j < N) op[(int64_t)j * ldo] = x;
-            if (amax != nullptr && m < M && n0 + j < N) lmax = fmaxf(lmax, fabsf(x));
+            for (int j = 0; j < 16; ++j) {
+              const float x = __uint_as_float(v[j]);
+              if (mok && n0 + j < N) op[(int64_t)j * ldo] = x;
+              if (amax != nullptr && m < M && n0 + j < N) lmax = fmaxf(lmax, fabsf(x));
+            }
           }
         }
       } else {
+        const int nch = ntile_w(nt) / 16;
 #pragma unroll 1
-        for (int c = 0; c < BN / 16; ++c) {
+        for (int c = 0; c < nch; ++c) {
           uint32_t acc[S][16];
 #pragma unroll
           for (int g = 0; g < S; ++g) tmem_ld16(tbase + g * BN + c * 16, acc[g]);
           tmem_ld_wait();
           const int n0 = nt * BN + c * 16;
+          if constexpr (RM) {
+            static_assert(sizeof(OutT) == 4, "row-major output is float32");
+            uint32_t v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float lo = 0.f;
+#pragma unroll
+              for (int g = S - 1; g >= 1; --g) lo = __fadd_rn(lo, __uint_as_float(acc[g][j]));
+              v[j] = __float_as_uint(__fmul_rn(__fadd_rn(__uint_as_float(acc[0][j]), lo), fscale));
+            }
+            if (mok) store_row16(reinterpret_cast<float*>(out) + (int64_t)m * ldo + n0, v, N - n0);
+            continue;
+          }
           OutT* op = out + (int64_t)n0 * ldo + m;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
@@ -447,7 +501,9 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                 double v = 0.0;
 #pragma unroll
                 for (int g = S - 1; g >= 1; --g) v += (double)__uint_as_float(acc[g][j]);
-                op[(int64_t)j * ldo] = ((double)hi + v) * scale;
+                const double r = ((double)hi + v) * scale;
+                double* o = &op[(int64_t)j * ldo];
+                *o = P.accum ? *o + r : r;
               }
               if (amax != nullptr && m < M && n0 + j < N)
                 lmax = fmaxf(lmax, fabsf(__fmul_rn(__fadd_rn(hi, lo), fscale)));
@@ -512,14 +568,44 @@ int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t row
   return r == CUDA_SUCCESS ? LNO_OT_OK : LNO_OT_ECUDA;
 }
 
+// Tiled map over float32 data of rank 3..5: dims innermost first, byte strides
+// of dims 1.., box extents; 64-byte swizzle when sw64 (box rows of 64 bytes),
+// zero fill beyond the dims.
+int make_f32_map(CUtensorMap* map, const void* base, int rank, const int64_t* dims,
+                 const int64_t* strides, const int* box, bool sw64) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return LNO_OT_ECUDA;
+  if (rank < 3 || rank > 5 || (reinterpret_cast<uintptr_t>(base) & 15) || (box[0] * 4) % 16 ||
+      (sw64 && box[0] * 4 != 64))
+    return LNO_OT_EINVAL;
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    if (dims[i] < 1 || box[i] < 1 || box[i] > 256) return LNO_OT_EINVAL;
+    d[i] = (cuuint64_t)dims[i];
+    bx[i] = (cuuint32_t)box[i];
+    es[i] = 1;
+    if (i > 0) {
+      if (strides[i - 1] % 16) return LNO_OT_EINVAL;
+      st[i - 1] = (cuuint64_t)strides[i - 1];
+    }
+  }
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base),
+                   d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? LNO_OT_OK : LNO_OT_ECUDA;
+}
+
 // mB must be maps with boxes of BN rows; mA boxes of 128 rows.
-template <int S, int BN, typename OutT, bool TF>
+template <int S, int BN, typename OutT, bool TF, bool RM>
 cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
                            int nprob, int M, int N, int ldo, double scale, int* flag,
                            unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag) {
   using C = Cfg<S, BN>;
   if (nprob <= 0 || M <= 0 || N <= 0) return cudaSuccess;
-  auto k = tc_gemm_sliced<S, BN, OutT, TF>;
+  if (RM && (ldo % 4 != 0 || ldo < ((N + 15) & ~15))) return cudaErrorInvalidValue;
+  auto k = tc_gemm_sliced<S, BN, OutT, TF, RM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   if (e != cudaSuccess) return e;
   const long long ntiles = (long long)nprob * ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
@@ -540,46 +626,38 @@ cudaError_t launch_sliced_product(int S, const CUtensorMap* mA, const CUtensorMa
                                   const TcProb* dp, int M, int N, double scale, int* flag,
                                   int nsm, cudaStream_t st, TcDiag dg) {
   switch (S) {
-    case 1: return launch_tc_gemm<1, 256, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
-    case 2: return launch_tc_gemm<2, 256, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
-    case 3: return launch_tc_gemm<3, 128, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
-    case 4: return launch_tc_gemm<4, 128, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
-    case 5: return launch_tc_gemm<5, 64, double>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    case 1: return launch_tc_gemm<1, 256, double, false, false>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    case 2: return launch_tc_gemm<2, 256, double, false, false>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    case 3: return launch_tc_gemm<3, 128, double, false, false>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    case 4: return launch_tc_gemm<4, 128, double, false, false>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
+    case 5: return launch_tc_gemm<5, 64, double, false, false>(mA, mB, dp, 1, M, N, M, scale, flag, nullptr, nsm, st, dg);
     default: return cudaErrorInvalidValue;
   }
 }
 long long tc_default_wait_cycles() { return kWaitCycles; }
 
-#define LNO_TC_INST(S, BN, T)                                                                   \
-  template cudaError_t launch_tc_gemm<S, BN, T, false>(const CUtensorMap*, const CUtensorMap*,  \
-                                                       const TcProb*, int, int, int, int, double, \
-                                                       int*, unsigned long long*, int,          \
-                                                       cudaStream_t, TcDiag);
-// W contractions (float32 output): slices x tile width
-LNO_TC_INST(2, 256, float)
-LNO_TC_INST(2, 128, float)
-LNO_TC_INST(3, 128, float)
-LNO_TC_INST(3, 64, float)
-LNO_TC_INST(4, 128, float)
-LNO_TC_INST(4, 96, float)
-LNO_TC_INST(4, 64, float)
-LNO_TC_INST(5, 64, float)
-LNO_TC_INST(1, 256, float)
-// DF assembly and the diagnostics (float64 output)
-LNO_TC_INST(1, 256, double)
-LNO_TC_INST(2, 256, double)
-LNO_TC_INST(3, 128, double)
-LNO_TC_INST(4, 128, double)
-LNO_TC_INST(5, 64, double)
-#undef LNO_TC_INST
+#define LNO_TC_INST(S, BN, T, TF, RM)                                                        \
+  template cudaError_t launch_tc_gemm<S, BN, T, TF, RM>(                                     \
+      const CUtensorMap*, const CUtensorMap*, const TcProb*, int, int, int, int, double, int*, \
+      unsigned long long*, int, cudaStream_t, TcDiag);
+// W contractions (float32 row-major output): slices x tile width
+LNO_TC_INST(2, 256, float, false, true)
+LNO_TC_INST(2, 128, float, false, true)
+LNO_TC_INST(3, 128, float, false, true)
+LNO_TC_INST(3, 64, float, false, true)
+LNO_TC_INST(4, 128, float, false, true)
+LNO_TC_INST(4, 96, float, false, true)
+LNO_TC_INST(4, 64, float, false, true)
+LNO_TC_INST(5, 64, float, false, true)
 // TF32 W contractions (2 TF32 slices, 3 products)
-template cudaError_t launch_tc_gemm<2, 256, float, true>(const CUtensorMap*, const CUtensorMap*,
-                                                         const TcProb*, int, int, int, int, double,
-                                                         int*, unsigned long long*, int,
-                                                         cudaStream_t, TcDiag);
-template cudaError_t launch_tc_gemm<2, 128, float, true>(const CUtensorMap*, const CUtensorMap*,
-                                                         const TcProb*, int, int, int, int, double,
-                                                         int*, unsigned long long*, int,
-                                                         cudaStream_t, TcDiag);
+LNO_TC_INST(2, 256, float, true, true)
+LNO_TC_INST(2, 128, float, true, true)
+// DF assembly and the diagnostics (float64 transposed output)
+LNO_TC_INST(1, 256, double, false, false)
+LNO_TC_INST(2, 256, double, false, false)
+LNO_TC_INST(3, 128, double, false, false)
+LNO_TC_INST(4, 128, double, false, false)
+LNO_TC_INST(5, 64, double, false, false)
+#undef LNO_TC_INST
 
 }  // namespace lno

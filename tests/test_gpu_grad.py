@@ -5,7 +5,11 @@ The oracle gradient is PyTorch autograd through the CPU float64 oracle,
 projected onto the inputs' symmetries exactly as the C ABI documents
 (dB symmetric in (p,q); dT2aa/bb antisymmetric in (i,j) and (a,b)).
 Tolerance: 1e-6 relative (element-wise against the largest entry of each
-gradient; directional derivatives against central differences, h = 1e-5).
+gradient; directional derivatives against central differences at h = 1e-5 and
+h/2, Richardson-extrapolated).  The float64 context runs the adjoint's
+contractions in float64; a BF16X10 context runs them on the tensor cores
+(tc_matmul: exact 4-slice BF16 operands, float64 output) and is held to the
+same tolerance.
 """
 import numpy as np
 import pytest
@@ -23,6 +27,13 @@ KEYS = ["B0", "B1", "e0", "e1", "t10", "t11", "t2aa", "t2bb", "t2ab"]
 @pytest.fixture(scope="module")
 def ctx64(lib):
     c = lno_ot.Context(0, "fp64")
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx10(lib):
+    c = lno_ot.Context(0, "bf16x10")
     yield c
     c.close()
 
@@ -84,6 +95,16 @@ def test_gradient_matches_oracle_small(ctx64, shape):
     compare(g, g_ref)
 
 
+@pytest.mark.parametrize("shape", [(9, 3, 2, 1), (20, 5, 3, 4), (40, 6, 5, 5)])
+def test_tensor_core_adjoint_matches_oracle_small(ctx10, shape):
+    nbas, na, nb, seed = shape
+    d = make_domain(nbas, (na, nb), naux=2 * nbas, L=nbas / 2, seed=seed, t1_sd=0.05)
+    g_ref, e_ref = oracle_grad(d)
+    g, e = gpu_grad(ctx10, d, gE=1.0)
+    assert abs(e - e_ref) <= 1e-9 * max(1.0, abs(e_ref))
+    compare(g, g_ref)
+
+
 def test_gradient_scales_with_gE(ctx64):
     d = make_domain(11, (3, 2), naux=22, L=6.0, seed=9, t1_sd=0.05)
     g1, _ = gpu_grad(ctx64, d, gE=1.0)
@@ -106,7 +127,7 @@ def test_c0_gradient_vs_oracle_and_central_differences(ctx64):
     def E(dm):
         return ctx64.energy(dm)["total"]
 
-    def perturbed(key, x, sign):
+    def perturbed(key, x, sign, h):
         dm = dict(dd, B=list(dd["B"]), eps=list(dd["eps"]), t1=list(dd["t1"]))
         xt = torch.as_tensor(x, device="cuda")
         if key in ("B0", "B1"):
@@ -129,16 +150,20 @@ def test_c0_gradient_vs_oracle_and_central_differences(ctx64):
         if key in ("t2aa", "t2bb"):
             x = x - x.transpose(1, 0, 2, 3)
             x = x - x.transpose(0, 1, 3, 2)
-        fd = (E(perturbed(key, x, +1)) - E(perturbed(key, x, -1))) / (2 * h)
+        fd1 = (E(perturbed(key, x, +1, h)) - E(perturbed(key, x, -1, h))) / (2 * h)
+        fd2 = (E(perturbed(key, x, +1, h / 2)) - E(perturbed(key, x, -1, h / 2))) / h
+        fd = (4 * fd2 - fd1) / 3
         an = float((g[ki] * torch.as_tensor(x)).sum())
-        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (key, fd, an)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (key, fd, an, fd1, fd2)
 
 
 def test_c4_subset_central_differences_all_nine_inputs(ctx64):
     # at the differentiation domain's size (nbas 200, 20/18 occupied): the
     # adjoint on a seeded triplet subset against central differences of the
-    # float64 forward on the same subset, h = 1e-5, along one random
-    # symmetry-respecting direction per input
+    # float64 forward on the same subset, along one random symmetry-respecting
+    # direction per input; central differences at h = 1e-5 and h/2 combined by
+    # Richardson extrapolation (the O(h^2) term cancels; a direction that moves
+    # every entry of an input at once has a large third derivative)
     d = config_domain("c4")
     rng = np.random.default_rng(2024)
     na, nb = d["nocc"]
@@ -151,7 +176,7 @@ def test_c4_subset_central_differences_all_nine_inputs(ctx64):
     def E(dm):
         return ctx64.energy(dm, trip_sel=sel)["total"]
 
-    def perturbed(key, x, sign):
+    def perturbed(key, x, sign, h):
         dm = dict(dd, B=list(dd["B"]), eps=list(dd["eps"]), t1=list(dd["t1"]))
         xt = torch.as_tensor(x, device="cuda")
         if key in ("B0", "B1"):
@@ -174,18 +199,33 @@ def test_c4_subset_central_differences_all_nine_inputs(ctx64):
         if key in ("t2aa", "t2bb"):
             x = x - x.transpose(1, 0, 2, 3)
             x = x - x.transpose(0, 1, 3, 2)
-        fd = (E(perturbed(key, x, +1)) - E(perturbed(key, x, -1))) / (2 * h)
+        fd1 = (E(perturbed(key, x, +1, h)) - E(perturbed(key, x, -1, h))) / (2 * h)
+        fd2 = (E(perturbed(key, x, +1, h / 2)) - E(perturbed(key, x, -1, h / 2))) / h
+        fd = (4 * fd2 - fd1) / 3
         an = float((g[ki] * torch.as_tensor(x)).sum())
-        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (key, fd, an)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (key, fd, an, fd1, fd2)
 
 
-def test_c4_subset_gradient_vs_oracle(ctx64):
+@pytest.fixture(scope="module")
+def c4_subset_oracle():
     d = config_domain("c4")
-    na, nb = d["nocc"]
     sel = [np.array([0, 500]), np.array([7]), np.array([1000]), np.array([3, 815])]
     g_ref, e_ref = oracle_grad(d, sel)
+    return d, sel, g_ref, e_ref
+
+
+def test_c4_subset_gradient_vs_oracle(ctx64, c4_subset_oracle):
+    d, sel, g_ref, e_ref = c4_subset_oracle
     g, e = gpu_grad(ctx64, d, sel)
     assert abs(e - e_ref) <= 1e-10 * abs(e_ref)
+    compare(g, g_ref)
+
+
+def test_c4_subset_tensor_core_adjoint_vs_oracle(ctx10, c4_subset_oracle):
+    d, sel, g_ref, e_ref = c4_subset_oracle
+    g, e = gpu_grad(ctx10, d, sel)
+    # the forward is the BF16X10 energy (float32 element arithmetic, ~1e-10 Eh per triplet)
+    assert abs(e - e_ref) <= 1e-8
     compare(g, g_ref)
 
 
