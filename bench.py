@@ -67,9 +67,10 @@ def peaks():
 # per-launch traffic scales with the launch's tensor flops at a fixed virtual
 # space.
 DRAM_BYTES_PER_TENSOR_FLOP = {
-    # tc_gemm_sliced<4,128,float>, nbas 368 nocc 8/6 naux 1200 group: 10.646 GB
-    # over 15 331 800 MMAs of 128x128x16 (profiles/tc_gemm_sliced_bf16x10_c1shape.md)
-    "bf16x10": 10.646e9 / (15331800 * 128 * 128 * 16 * 2),
+    # tc_gemm_sliced<4,128,float,row-major>, nbas 368 nocc 8/6 naux 1200 group:
+    # 10.642 GB over 15 331 800 MMAs of 128x128x16
+    # (profiles/tc_gemm_sliced_bf16x10_c1shape.md)
+    "bf16x10": 10.642e9 / (15331800 * 128 * 128 * 16 * 2),
 }
 
 # FP32 operations per restricted (abc) element in the float32 energy kernel
@@ -401,6 +402,7 @@ def run_backward(args):
     ctx.backward(dd, 1.0, g, trip_sel=sel)
     torch.cuda.synchronize()
     t_bwd = time.perf_counter() - t0
+    bst = ctx.stats()
     t0 = time.perf_counter()
     ctx.energy(dd, trip_sel=sel)
     torch.cuda.synchronize()
@@ -422,6 +424,11 @@ def run_backward(args):
             "backward_over_forward": t_bwd / t_fwd,
             "sample_algorithmic_flops": flops,
             "forward_breakdown_ms": {k: fst[k] for k in ("ms_stage", "ms_contract", "ms_energy")},
+            "backward_breakdown_ms": {
+                "ms_total": bst["ms_total"],
+                "ms_stage_and_operand_build": bst["ms_stage"],
+                "ms_contractions": bst["ms_contract"],
+                "ms_energy_adjoint": bst["ms_energy"]},
             "w_recomputed_per_triplet": True}
     print(json.dumps(line), flush=True)
     return 0

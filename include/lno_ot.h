@@ -243,7 +243,14 @@ LNO_OT_API int lno_ot_energy_batched(lno_ot_ctx* ctx, int ndom, const lno_ot_dom
                           lno_ot_result* out);
 
 /* Adjoint of lno_ot_energy: g = gE * dE(T)/d(B, eps, T1, T2), W recomputed
- * per triplet (never stored).  Runs in float64. */
+ * per triplet (never stored).  Operands, energy adjoint and layout adjoints
+ * run in float64; the contractions (the DF assembly, the X recompute, the
+ * contraction and DF adjoints) run in float64 in an LNO_OT_FP64 context and on
+ * the tensor cores otherwise (4 exact BF16 slices of each float64 operand with
+ * a power-of-two scale, float64 output of the exact class sums).  Stats of the
+ * call (lno_ot_last_stats): ms_total wall clock, ms_stage staging and operand
+ * builds, ms_contract the contraction kernels (tensor-core context), ms_energy
+ * the energy adjoint kernels. */
 LNO_OT_API int lno_ot_backward(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE,
                     lno_ot_grad* g);
 

@@ -127,10 +127,17 @@ struct TcSeg {
   int neg;          // 1: subtract this segment
 };
 
+// TcProb.flags: kTcAccum adds the result to out instead of storing it;
+// kTcFloatRest forms the float64 result as HI + the float32 sum of the lower
+// weight classes, scaled in float32 (the scale must be a power of two): two
+// float64 operations per element instead of six, ~2^-32 relative instead of
+// the exact class sums (used by the adjoint's products)
+constexpr int kTcAccum = 1, kTcFloatRest = 2;
+
 struct TcProb {
   TcSeg seg[kMaxSeg];
   int nseg;
-  int accum;        // float64 transposed output only: 1 adds to out instead of storing
+  int flags;        // float64 transposed output only: kTcAccum, kTcFloatRest
   void* out;        // output of this problem: [N][ldo] (transposed) or [M][ldo] (row-major)
 };
 

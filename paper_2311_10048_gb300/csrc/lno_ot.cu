@@ -70,6 +70,8 @@ cudaError_t launch_transpose_t2ab(const double*, int, int, int, int, double*, cu
 cudaError_t launch_absmax(const double*, int64_t, unsigned long long*, cudaStream_t);
 cudaError_t launch_view_absmax(const double* in, int64_t rs, int64_t ks, int rows, int K,
                                unsigned long long* out, cudaStream_t s);
+cudaError_t launch_sum_partials(const double* part, int nsp, int M, int N, double* C,
+                                int64_t ldc, bool accum, cudaStream_t s);
 template <int S>
 cudaError_t launch_view_slices(const double* in, int64_t rs, int64_t ks, int rows, int K,
                                int Kp, __nv_bfloat16* out, int64_t slice_stride, double inv,
@@ -299,6 +301,16 @@ cudaError_t launch_contract(int S, bool tf, int bn_req, const Operand& A0, const
 #undef LNO_CALL
 }
 
+// Strided float64 view: element (r, k) at p[r rs + k ks].
+struct View {
+  const double* p;
+  int64_t rs, ks;
+};
+constexpr int64_t kMaxSplit = 64;   // K chunks of one tc_matmul
+struct Run;
+int tc_matmul(Run& R, Arena& A, int M, int N, int K, View a, View b, double* C, int64_t ldc,
+              double alpha, bool accum);
+
 struct Run {
   lno_ot_ctx* ctx;
   const lno_ot_domain* dom;
@@ -390,6 +402,9 @@ struct Run {
          int ldo) {
     if (M <= 0 || N <= 0) return LNO_OT_OK;
     stats->other_launches++;
+    if (f64 && tc_adjoint)   // adjoint of a tensor-core precision: float64 blocks, TC product
+      return tc_matmul(*this, arena, N, M, naux, View{Ro.f64 + r0 * Ro.Kp, Ro.Kp, 1},
+                       View{Lo.f64 + l0 * Lo.Kp, Lo.Kp, 1}, out, ldo, 1.0, false);
     if (f64) {
       ProbF64 p{};
       p.nseg = 1;
@@ -1744,12 +1759,6 @@ int zero_operand_like(Arena& A, const Operand& src, Operand& d, cudaStream_t st)
   return zeros(A, &d.f64, n, st);
 }
 
-// Strided float64 view: element (r, k) at p[r rs + k ks].
-struct View {
-  const double* p;
-  int64_t rs, ks;
-};
-
 // C[m ldc + n] (+)= alpha sum_k a(m, k) b(n, k) on the tensor cores: both views
 // are cut into 4 exact BF16 slices with power-of-two scales (the DF assembly's
 // representation, 10 slice products, float64 output of the exact class sums).
@@ -1759,6 +1768,8 @@ int tc_matmul(Run& R, Arena& A, int M, int N, int K, View a, View b, double* C, 
   if (M <= 0 || N <= 0 || K <= 0) return LNO_OT_OK;
   constexpr int S = 4;
   cudaStream_t st = R.st;
+  cudaEvent_t e0 = R.event(), e1 = R.event();
+  if (e0) cudaEventRecord(e0, st);
   unsigned long long* am = R.ctx->d_amax;
   CU(cudaMemsetAsync(am, 0, 2 * sizeof(unsigned long long), st));
   CU(launch_view_absmax(a.p, a.rs, a.ks, M, K, am, st));
@@ -1781,36 +1792,68 @@ int tc_matmul(Run& R, Arena& A, int M, int N, int K, View a, View b, double* C, 
     return std::ldexp(1.0, f == 0.5 ? e - 1 : e);
   };
   const double sa = pow2_at_least(amax[0]), sb = pow2_at_least(amax[1]);
-  const int64_t Kp = round_up(K, 8);
+  // Split K when the output has few 128 x 128 tiles (a long contraction onto a
+  // short output: the contraction adjoints over the pair rows, the DF adjoints
+  // over v^2 rows): chunk c is problem c of one launch, writing its own float64
+  // partial; the partials are added into C in chunk order.
+  const int64_t tiles = (int64_t)ceil_div(N, 128) * ceil_div(M, 128);
+  int nsp = 1;
+  if (tiles < 2 * R.ctx->nsm && K >= 4096)
+    nsp = (int)std::max<int64_t>(1, std::min<int64_t>({ceil_div(4 * R.ctx->nsm, tiles),
+                                                       K / 2048, kMaxSplit}));
+  const int Kc = (int)round_up(ceil_div(K, nsp), 32);
+  nsp = ceil_div(K, Kc);
+  const int64_t Kp = round_up(Kc, 8);
   __nv_bfloat16 *qa, *qb;
-  TRY(A.get(&qa, (size_t)(S * M * Kp)));
-  TRY(A.get(&qb, (size_t)(S * N * Kp)));
-  CU(launch_view_slices<S>(a.p, a.rs, a.ks, M, K, (int)Kp, qa, (int64_t)M * Kp, 128.0 / sa, st));
-  CU(launch_view_slices<S>(b.p, b.rs, b.ks, N, K, (int)Kp, qb, (int64_t)N * Kp, 128.0 / sb, st));
+  TRY(A.get(&qa, (size_t)(S * nsp * M * Kp)));
+  TRY(A.get(&qb, (size_t)(S * nsp * N * Kp)));
+  for (int c = 0; c < nsp; ++c) {
+    const int k0 = c * Kc, kc = std::min(Kc, K - k0);
+    CU(launch_view_slices<S>(a.p + k0 * a.ks, a.rs, a.ks, M, kc, (int)Kp, qa + c * M * Kp,
+                             (int64_t)nsp * M * Kp, 128.0 / sa, st));
+    CU(launch_view_slices<S>(b.p + k0 * b.ks, b.rs, b.ks, N, kc, (int)Kp, qb + c * N * Kp,
+                             (int64_t)nsp * N * Kp, 128.0 / sb, st));
+  }
   // the kernel writes its output transposed: its rows (A role) are n, its
   // columns (B role) m, so out[m ldc + n]
   CUtensorMap mA[2], mB[2];
-  TRY(make_operand_map(&mA[0], qb, Kp, N, S, (int64_t)N * Kp, 128));
-  TRY(make_operand_map(&mB[0], qa, Kp, M, S, (int64_t)M * Kp, 128));
+  TRY(make_operand_map(&mA[0], qb, Kp, (int64_t)nsp * N, S, (int64_t)nsp * N * Kp, 128));
+  TRY(make_operand_map(&mB[0], qa, Kp, (int64_t)nsp * M, S, (int64_t)nsp * M * Kp, 128));
   mA[1] = mA[0];
   mB[1] = mB[0];
-  TcProb p{};
-  p.nseg = 1;
-  p.seg[0] = TcSeg{0, 0, 0, 0, K, alpha < 0 ? 1 : 0};
-  p.accum = accum ? 1 : 0;
-  p.out = C;
-  TcProb* dp;
-  TRY(A.get(&dp, 1));
-  CU(cudaMemcpyAsync(dp, &p, sizeof p, cudaMemcpyHostToDevice, st));
+  double* part = nullptr;
+  if (nsp > 1) TRY(A.get(&part, (size_t)nsp * M * N));
+  // the float32 rest scales in float32: |alpha| must be a power of two (the
+  // adjoint's products use +-1)
+  int ex;
+  if (std::frexp(std::fabs(alpha), &ex) != 0.5) return LNO_OT_EINVAL;
   const double scale = sa * sb * std::ldexp(1.0, -14) * std::fabs(alpha);
-  CU((launch_tc_gemm<4, 128, double, false, false>(mA, mB, dp, 1, N, M, (int)ldc, scale,
+  // products of the class sums with the scale stay normal floats
+  const bool float_rest = scale >= std::ldexp(1.0, -100) && scale <= std::ldexp(1.0, 100);
+  std::vector<TcProb> pv(nsp);
+  for (int c = 0; c < nsp; ++c) {
+    TcProb& p = pv[c];
+    p.nseg = 1;
+    p.seg[0] = TcSeg{0, 0, c * N, c * M, std::min(Kc, K - c * Kc), alpha < 0 ? 1 : 0};
+    p.flags = (float_rest ? kTcFloatRest : 0) | (nsp == 1 && accum ? kTcAccum : 0);
+    p.out = nsp == 1 ? C : part + (int64_t)c * M * N;
+  }
+  TcProb* dp;
+  TRY(A.get(&dp, (size_t)nsp));
+  CU(cudaMemcpyAsync(dp, pv.data(), nsp * sizeof(TcProb), cudaMemcpyHostToDevice, st));
+  CU((launch_tc_gemm<4, 128, double, false, false>(mA, mB, dp, nsp, N, M,
+                                                   nsp == 1 ? (int)ldc : N, scale,
                                                    R.ctx->d_flag, nullptr, R.ctx->nsm, st,
                                                    tc_normal())));
+  if (nsp > 1) CU(launch_sum_partials(part, nsp, M, N, C, ldc, accum, st));
+  if (e1) cudaEventRecord(e1, st);
+  if (e0 && e1) R.contract_ev.push_back({e0, e1});
   R.stats->contract_launches++;
-  R.stats->other_launches += 4;
+  R.stats->other_launches += 3 + 2 * nsp;
   A.drop(qa);
   A.drop(qb);
   A.drop(dp);
+  if (part) A.drop(part);
   return LNO_OT_OK;
 }
 
@@ -2001,8 +2044,12 @@ int backward_spin(SpinPass& P, GradAcc& G, double gE) {
       CU(cudaMemsetAsync(dX, 0, (size_t)ng * N1 * P1 * sizeof(double), st));
       if (is_mixed) CU(cudaMemsetAsync(dZ, 0, (size_t)ng * N2 * P2 * sizeof(double), st));
       ea.trips = dtrips + g0;
+      cudaEvent_t ee0 = R.event(), ee1 = R.event();
+      if (ee0) cudaEventRecord(ee0, st);
       CU(launch_energy_backward(ea, X, Z, dX, dZ, G.dt1[s], G.dt1[is_mixed ? t : s], dovss,
                                 dovts, G.deps[s], G.deps[is_mixed ? t : s], gE, ng, Pch, st));
+      if (ee1) cudaEventRecord(ee1, st);
+      if (ee0 && ee1) R.energy_ev.push_back({ee0, ee1});
       if (R.fov[0]) {  // the f_ov part: planes are T2 amplitudes, coefficients f_ov
         EnergyArgs ef = ea;
         ef.vmode = 1;
@@ -2191,9 +2238,15 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
   // cores through tc_matmul
   R.tc_adjoint = ctx->prec != LNO_OT_FP64;
   CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+  // wall-clock phases (the stream is synchronised at each boundary)
+  using clk = std::chrono::steady_clock;
+  const auto w0 = clk::now();
+  double wbuild = 0.0;
   CaseSel cs[4];
   for (int c = 0; c < 4; ++c) TRY(select_case(dom, c, cs[c]));
   TRY(R.stage());
+  CU(cudaStreamSynchronize(R.st));
+  const double wstage = std::chrono::duration<double, std::milli>(clk::now() - w0).count();
   if (!R.fov[0] && (g->dfov[0] || g->dfov[1])) {
     // dE/df_ov at f_ov = 0 (E is affine in f_ov): run the f_ov pass on zeros
     for (int s = 0; s < 2; ++s) {
@@ -2233,10 +2286,13 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
     SpinPass P(R, s, s == 0 ? cs[0] : cs[3], s == 0 ? cs[1] : cs[2], e_dummy[s == 0 ? 0 : 3],
                e_dummy[s == 0 ? 1 : 2]);
     if (P.same.trips.empty() && P.mixed.trips.empty()) continue;
+    const auto b0 = clk::now();
     P.plan();
     TRY(P.prepare_inputs());
     TRY(P.build_v_blocks());
     TRY(P.build());
+    CU(cudaStreamSynchronize(R.st));
+    wbuild += std::chrono::duration<double, std::milli>(clk::now() - b0).count();
     TRY(backward_spin(P, G, gE));
     CU(cudaStreamSynchronize(R.st));
   }
@@ -2260,7 +2316,23 @@ int backward_impl(lno_ot_ctx* ctx, const lno_ot_domain* dom, double gE, lno_ot_g
   CU(cudaStreamSynchronize(R.st));
   int flag = 0;
   CU(cudaMemcpy(&flag, ctx->d_flag, sizeof flag, cudaMemcpyDeviceToHost));
-  return flag ? LNO_OT_ETIMEOUT : LNO_OT_OK;
+  if (flag) return LNO_OT_ETIMEOUT;
+  // stats of the adjoint: ms_total wall clock, ms_stage the staging plus the
+  // operand and V-block builds (their DF assembly), ms_contract the event time
+  // of its contractions (tensor-core products or float64 GEMMs), ms_energy the
+  // energy adjoint kernels
+  ctx->stats.ms_total = std::chrono::duration<double, std::milli>(clk::now() - w0).count();
+  ctx->stats.ms_stage = wstage + wbuild;
+  float ms = 0;
+  double acc = 0;
+  for (auto& p : R.contract_ev)
+    if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) acc += ms;
+  ctx->stats.ms_contract = acc;
+  acc = 0;
+  for (auto& p : R.energy_ev)
+    if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) acc += ms;
+  ctx->stats.ms_energy = acc;
+  return LNO_OT_OK;
 }
 
 }  // namespace

@@ -28,6 +28,7 @@
 // s1 an integer in [-128, 128], s2 a multiple of 2^-8 in [-1/2, 1/2], ...,
 // each step rounded to nearest).
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 
@@ -257,10 +258,56 @@ __global__ void view_absmax(const double* __restrict__ in, int64_t rs, int64_t k
   if ((tx & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
+// round(v 2^e2) to nearest (ties to even) from the bits of v, in integer
+// arithmetic (this GPU's float64 rate is 1/64 of its float32 rate); |v 2^e2|
+// must stay below 2^62, v finite.
+__device__ __forceinline__ int64_t round_scaled(double v, int e2) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  uint64_t m = b & ((1ull << 52) - 1);
+  if (ex != 0) m |= 1ull << 52;
+  const int sh = (ex == 0 ? 1 : ex) - 1075 + e2;   // |v| 2^e2 = m 2^sh
+  uint64_t q;
+  if (m == 0) {
+    q = 0;
+  } else if (sh >= 0) {
+    q = m << sh;
+  } else if (-sh > 54) {
+    q = 0;                                        // m 2^sh < 1/2
+  } else {
+    const int r = -sh;
+    const uint64_t rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+    q = m >> r;
+    if (rem > half || (rem == half && (q & 1))) ++q;
+  }
+  return (b >> 63) ? -(int64_t)q : (int64_t)q;
+}
+
+// The same exact slices as StoreSlices, from one rounding of the scaled value
+// to S * 8 - 1 fractional bits followed by integer digit extraction (base 256,
+// each digit rounded half up, so |s_0| <= 128 and |s_q 2^(8q)| <= 128):
+// value = 2^-e7 (s_0 + ... + s_{S-1}), e7 = e2 - 8 (S - 1), e2 passed in.
+template <int S>
+struct StoreSlicesInt {
+  __nv_bfloat16* p;
+  int64_t slice_stride;
+  int e2;   // log2(2^7 / scale) + 8 (S - 1)
+  __device__ __forceinline__ void operator()(int64_t idx, double v) const {
+    int64_t R = round_scaled(v, e2);
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      const int sh = 8 * (S - 1 - q);
+      const int64_t d = sh ? (R + (1ll << (sh - 1))) >> sh : R;
+      R -= d << sh;
+      p[q * slice_stride + idx] = __float2bfloat16_rn(ldexpf((float)d, -8 * q));
+    }
+  }
+};
+
 // view -> S BF16 slices [s][r][Kp] (k-contiguous rows, zero for k >= K)
 template <int S>
 __global__ void view_slices(const double* __restrict__ in, int64_t rs, int64_t ks, int rows,
-                            int K, int Kp, StoreSlices<S> st) {
+                            int K, int Kp, StoreSlicesInt<S> st) {
   __shared__ double t[32][33];   // [k][r]
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool rfast = ks != 1 && rs == 1;
@@ -275,9 +322,23 @@ __global__ void view_slices(const double* __restrict__ in, int64_t rs, int64_t k
     __syncthreads();
     for (int i = ty; i < 32; i += 8) {
       const int r = r0 + i, k = k0 + tx;
-      if (r < rows && k < Kp) st((int64_t)r * Kp + k, t[tx][i], 1);
+      if (r < rows && k < Kp) st((int64_t)r * Kp + k, t[tx][i]);
     }
     __syncthreads();
+  }
+}
+
+// C[m ldc + n] = (accum ? C : 0) + sum over c of part[c][m][n], in chunk order.
+__global__ void sum_partials(const double* __restrict__ part, int nsp, int M, int N,
+                             double* __restrict__ C, int64_t ldc, int accum) {
+  const int64_t n_all = (int64_t)M * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_all;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = i / N, n = i - m * N;
+    double v = 0.0;
+    for (int c = 0; c < nsp; ++c) v += part[(int64_t)c * n_all + i];
+    double* o = C + m * ldc + n;
+    *o = accum ? *o + v : v;
   }
 }
 
@@ -457,6 +518,14 @@ cudaError_t launch_absmax(const double* x, int64_t n, unsigned long long* out, c
   return cudaGetLastError();
 }
 
+cudaError_t launch_sum_partials(const double* part, int nsp, int M, int N, double* C,
+                                int64_t ldc, bool accum, cudaStream_t s) {
+  const int64_t n = (int64_t)M * N;
+  if (n <= 0) return cudaSuccess;
+  sum_partials<<<grid_for(n), 256, 0, s>>>(part, nsp, M, N, C, ldc, accum ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_view_absmax(const double* in, int64_t rs, int64_t ks, int rows, int K,
                                unsigned long long* out, cudaStream_t s) {
   if (rows <= 0 || K <= 0) return cudaSuccess;
@@ -465,14 +534,17 @@ cudaError_t launch_view_absmax(const double* in, int64_t rs, int64_t ks, int row
   return cudaGetLastError();
 }
 
+// inv = 2^7 / scale, a power of two
 template <int S>
 cudaError_t launch_view_slices(const double* in, int64_t rs, int64_t ks, int rows, int K,
                                int Kp, __nv_bfloat16* out, int64_t slice_stride, double inv,
                                cudaStream_t s) {
   if (rows <= 0 || Kp <= 0) return cudaSuccess;
+  int e;
+  if (!(inv > 0) || std::frexp(inv, &e) != 0.5) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)std::min((rows + 31) / 32, 4096));
-  view_slices<S><<<grid, dim3(32, 8), 0, s>>>(in, rs, ks, rows, K, Kp,
-                                               StoreSlices<S>{out, slice_stride, inv, inv});
+  view_slices<S><<<grid, dim3(32, 8), 0, s>>>(
+      in, rs, ks, rows, K, Kp, StoreSlicesInt<S>{out, slice_stride, (e - 1) + 8 * (S - 1)});
   return cudaGetLastError();
 }
 template cudaError_t launch_view_slices<4>(const double*, int64_t, int64_t, int, int, int,

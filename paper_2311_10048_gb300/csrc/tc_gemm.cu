@@ -460,6 +460,43 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
             }
           }
         }
+      } else if constexpr (RM && BN <= 128) {
+        // the class accumulators fill TMEM: combine the whole row into
+        // registers, free TMEM for the next tile's MMAs, then store
+        static_assert(sizeof(OutT) == 4, "row-major output is float32");
+        const int nch = ntile_w(nt) / 16;
+        uint32_t v[BN];
+#pragma unroll
+        for (int c = 0; c < BN / 16; ++c) {
+          if (c < nch) {
+            uint32_t acc[S][16];
+#pragma unroll
+            for (int g = 0; g < S; ++g) tmem_ld16(tbase + g * BN + c * 16, acc[g]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float lo = 0.f;
+#pragma unroll
+              for (int g = S - 1; g >= 1; --g) lo = __fadd_rn(lo, __uint_as_float(acc[g][j]));
+              v[c * 16 + j] =
+                  __float_as_uint(__fmul_rn(__fadd_rn(__uint_as_float(acc[0][j]), lo), fscale));
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(tempty);
+        if (mok) {
+          float* orow = reinterpret_cast<float*>(out) + (int64_t)m * ldo + nt * BN;
+#pragma unroll
+          for (int c = 0; c < BN / 16; ++c) {
+            if (c < nch) {
+              uint32_t w[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) w[j] = v[c * 16 + j];
+              store_row16(orow + c * 16, w, N - nt * BN - c * 16);
+            }
+          }
+        }
       } else {
         const int nch = ntile_w(nt) / 16;
 #pragma unroll 1
@@ -498,12 +535,17 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
               // float64 output: the exact class sums added in float64 (smallest
               // first), so the output keeps ~53 bits instead of HI + a float32 rest
               if (mok && n0 + j < N) {
-                double v = 0.0;
+                double r;
+                if (P.flags & kTcFloatRest) {
+                  r = (double)__fmul_rn(hi, fscale) + (double)__fmul_rn(lo, fscale);
+                } else {
+                  double v = 0.0;
 #pragma unroll
-                for (int g = S - 1; g >= 1; --g) v += (double)__uint_as_float(acc[g][j]);
-                const double r = ((double)hi + v) * scale;
+                  for (int g = S - 1; g >= 1; --g) v += (double)__uint_as_float(acc[g][j]);
+                  r = ((double)hi + v) * scale;
+                }
                 double* o = &op[(int64_t)j * ldo];
-                *o = P.accum ? *o + r : r;
+                *o = (P.flags & kTcAccum) ? *o + r : r;
               }
               if (amax != nullptr && m < M && n0 + j < N)
                 lmax = fmaxf(lmax, fabsf(__fmul_rn(__fadd_rn(hi, lo), fscale)));
@@ -570,7 +612,9 @@ int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t row
 
 // Tiled map over float32 data of rank 3..5: dims innermost first, byte strides
 // of dims 1.., box extents; 64-byte swizzle when sw64 (box rows of 64 bytes),
-// zero fill beyond the dims.
+// zero fill beyond the dims.  No L2 promotion: the boxes' 64-byte rows lie 1-2
+// KB apart, and a promoted 256-byte fetch would bring in columns that other
+// tiles use much later.
 int make_f32_map(CUtensorMap* map, const void* base, int rank, const int64_t* dims,
                  const int64_t* strides, const int* box, bool sw64) {
   EncodeTiledFn enc = get_encode();
@@ -593,7 +637,7 @@ int make_f32_map(CUtensorMap* map, const void* base, int rank, const int64_t* di
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base),
                    d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? LNO_OT_OK : LNO_OT_ECUDA;
 }
 
