@@ -309,7 +309,17 @@ struct View {
 constexpr int64_t kMaxSplit = 64;   // K chunks of one tc_matmul
 struct Run;
 int tc_matmul(Run& R, Arena& A, int M, int N, int K, View a, View b, double* C, int64_t ldc,
-              double alpha, bool accum);
+              double alpha, bool accum, bool b_const = false);
+
+// Slices of a read-only view kept by tc_matmul for the rest of a Run (the DF
+// factor blocks that every slot's DF adjoint multiplies).
+struct SliceCacheEntry {
+  const double* p;
+  int64_t rs, ks;
+  int rows, K, Kc, nsp;
+  __nv_bfloat16* q;
+  double sigma;
+};
 
 struct Run {
   lno_ot_ctx* ctx;
@@ -337,6 +347,7 @@ struct Run {
   Operand Boo[2], Bov[2], Bvv[2];
   const double* fov[2] = {nullptr, nullptr};  // f_ov blocks (both or none)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> contract_ev, energy_ev;
+  std::vector<SliceCacheEntry> slice_cache;   // tc_matmul, read-only B views
   lno_ot_stats* stats;
 
   Run(lno_ot_ctx* c, const lno_ot_domain* d)
@@ -1764,34 +1775,12 @@ int zero_operand_like(Arena& A, const Operand& src, Operand& d, cudaStream_t st)
 // representation, 10 slice products, float64 output of the exact class sums).
 // Used by the adjoint of the tensor-core precisions.
 int tc_matmul(Run& R, Arena& A, int M, int N, int K, View a, View b, double* C, int64_t ldc,
-              double alpha, bool accum) {
+              double alpha, bool accum, bool b_const) {
   if (M <= 0 || N <= 0 || K <= 0) return LNO_OT_OK;
   constexpr int S = 4;
   cudaStream_t st = R.st;
   cudaEvent_t e0 = R.event(), e1 = R.event();
   if (e0) cudaEventRecord(e0, st);
-  unsigned long long* am = R.ctx->d_amax;
-  CU(cudaMemsetAsync(am, 0, 2 * sizeof(unsigned long long), st));
-  CU(launch_view_absmax(a.p, a.rs, a.ks, M, K, am, st));
-  CU(launch_view_absmax(b.p, b.rs, b.ks, N, K, am + 1, st));
-  unsigned long long hb[2];
-  CU(cudaMemcpyAsync(hb, am, sizeof hb, cudaMemcpyDeviceToHost, st));
-  CU(cudaStreamSynchronize(st));
-  double amax[2];
-  std::memcpy(amax, hb, sizeof amax);
-  if (!std::isfinite(amax[0]) || !std::isfinite(amax[1])) return LNO_OT_EINVAL;
-  if (amax[0] == 0.0 || amax[1] == 0.0) {   // a zero operand: nothing to add
-    if (!accum)
-      for (int m = 0; m < M; ++m)
-        CU(cudaMemsetAsync(C + (int64_t)m * ldc, 0, (size_t)N * sizeof(double), st));
-    return LNO_OT_OK;
-  }
-  auto pow2_at_least = [](double x) {
-    int e;
-    const double f = std::frexp(x, &e);
-    return std::ldexp(1.0, f == 0.5 ? e - 1 : e);
-  };
-  const double sa = pow2_at_least(amax[0]), sb = pow2_at_least(amax[1]);
   // Split K when the output has few 128 x 128 tiles (a long contraction onto a
   // short output: the contraction adjoints over the pair rows, the DF adjoints
   // over v^2 rows): chunk c is problem c of one launch, writing its own float64
@@ -1804,16 +1793,53 @@ int tc_matmul(Run& R, Arena& A, int M, int N, int K, View a, View b, double* C, 
   const int Kc = (int)round_up(ceil_div(K, nsp), 32);
   nsp = ceil_div(K, Kc);
   const int64_t Kp = round_up(Kc, 8);
-  __nv_bfloat16 *qa, *qb;
+  // a read-only B view sliced before with the same chunking
+  const SliceCacheEntry* hit = nullptr;
+  if (b_const)
+    for (const auto& e : R.slice_cache)
+      if (e.p == b.p && e.rs == b.rs && e.ks == b.ks && e.rows == N && e.K == K && e.Kc == Kc &&
+          e.nsp == nsp)
+        hit = &e;
+  unsigned long long* am = R.ctx->d_amax;
+  CU(cudaMemsetAsync(am, 0, 2 * sizeof(unsigned long long), st));
+  CU(launch_view_absmax(a.p, a.rs, a.ks, M, K, am, st));
+  if (!hit) CU(launch_view_absmax(b.p, b.rs, b.ks, N, K, am + 1, st));
+  unsigned long long hb[2];
+  CU(cudaMemcpyAsync(hb, am, sizeof hb, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  double amax[2];
+  std::memcpy(amax, hb, sizeof amax);
+  if (hit) amax[1] = hit->sigma;
+  if (!std::isfinite(amax[0]) || !std::isfinite(amax[1])) return LNO_OT_EINVAL;
+  if (amax[0] == 0.0 || amax[1] == 0.0) {   // a zero operand: nothing to add
+    if (!accum)
+      for (int m = 0; m < M; ++m)
+        CU(cudaMemsetAsync(C + (int64_t)m * ldc, 0, (size_t)N * sizeof(double), st));
+    return LNO_OT_OK;
+  }
+  auto pow2_at_least = [](double x) {
+    int e;
+    const double f = std::frexp(x, &e);
+    return std::ldexp(1.0, f == 0.5 ? e - 1 : e);
+  };
+  const double sa = pow2_at_least(amax[0]), sb = hit ? hit->sigma : pow2_at_least(amax[1]);
+  __nv_bfloat16 *qa, *qb = hit ? hit->q : nullptr;
   TRY(A.get(&qa, (size_t)(S * nsp * M * Kp)));
-  TRY(A.get(&qb, (size_t)(S * nsp * N * Kp)));
+  if (!qb) {
+    if (b_const)
+      TRY(R.arena.get(&qb, (size_t)(S * nsp * N * Kp)));
+    else
+      TRY(A.get(&qb, (size_t)(S * nsp * N * Kp)));
+  }
   for (int c = 0; c < nsp; ++c) {
     const int k0 = c * Kc, kc = std::min(Kc, K - k0);
     CU(launch_view_slices<S>(a.p + k0 * a.ks, a.rs, a.ks, M, kc, (int)Kp, qa + c * M * Kp,
                              (int64_t)nsp * M * Kp, 128.0 / sa, st));
-    CU(launch_view_slices<S>(b.p + k0 * b.ks, b.rs, b.ks, N, kc, (int)Kp, qb + c * N * Kp,
-                             (int64_t)nsp * N * Kp, 128.0 / sb, st));
+    if (!hit)
+      CU(launch_view_slices<S>(b.p + k0 * b.ks, b.rs, b.ks, N, kc, (int)Kp, qb + c * N * Kp,
+                               (int64_t)nsp * N * Kp, 128.0 / sb, st));
   }
+  if (b_const && !hit) R.slice_cache.push_back({b.p, b.rs, b.ks, N, K, Kc, nsp, qb, sb});
   // the kernel writes its output transposed: its rows (A role) are n, its
   // columns (B role) m, so out[m ldc + n]
   CUtensorMap mA[2], mB[2];
@@ -1851,7 +1877,7 @@ int tc_matmul(Run& R, Arena& A, int M, int N, int K, View a, View b, double* C, 
   R.stats->contract_launches++;
   R.stats->other_launches += 3 + 2 * nsp;
   A.drop(qa);
-  A.drop(qb);
+  if (!b_const) A.drop(qb);
   A.drop(dp);
   if (part) A.drop(part);
   return LNO_OT_OK;
@@ -1865,9 +1891,9 @@ int df_adjoint(Run& R, Arena& A, const Operand& Lo, Operand& dL, int64_t l0, int
   if (R.tc_adjoint) {
     // dL[l0+m][Q] += sum_n dout[n][m] R[r0+n][Q];  dR[r0+n][Q] += sum_m dout[n][m] L[l0+m][Q]
     TRY(tc_matmul(R, A, M, R.naux, N, View{dout, 1, ldo}, View{Ro.f64 + r0 * Qp, 1, Qp},
-                  dL.f64 + l0 * Qp, Qp, 1.0, true));
+                  dL.f64 + l0 * Qp, Qp, 1.0, true, true));
     TRY(tc_matmul(R, A, N, R.naux, M, View{dout, ldo, 1}, View{Lo.f64 + l0 * Qp, 1, Qp},
-                  dR.f64 + r0 * Qp, Qp, 1.0, true));
+                  dR.f64 + r0 * Qp, Qp, 1.0, true, true));
     return LNO_OT_OK;
   }
   GemmS g[2];
