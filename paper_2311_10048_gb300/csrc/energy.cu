@@ -476,6 +476,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   // the 16-byte chunk (t & 3) of sub-cube row R = 64 u + (t >> 2), so four
   // neighbouring lanes read one 64-byte row and a warp reads 8 whole rows per
   // load instruction.  okm bit (3 u + cube) marks the valid rows.
+  int3 blkf;   // cube tile of the last fetch (prefetched with its data)
   auto fetch = [&](int gq, int q) {
     const Trip tr = a.trips[gq];
     const float* Xg = X + (int64_t)gq * a.x_stride;
@@ -485,6 +486,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
     (void)Zg;
     (void)Vf;
     const int3 blk = a.blocks[q];
+    blkf = blk;
     const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
     const int ch = (tid & 3) * 4;
     okm = 0;
@@ -633,7 +635,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   }
   fetch(g, q);
   for (;;) {
-    const int3 blk = a.blocks[q];
+    const int3 blk = blkf;
     const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
     if constexpr (TM) {   // this tile's sub-cubes
       const int st = (int)(it & 1u);
