@@ -342,6 +342,17 @@ LNO_OT_API int lno_ot_selftest_gemm(int device, int S, int M, int N, int K, cons
 LNO_OT_API int lno_ot_selftest_timeout(int device, long long wait_cycles, int* code,
                                        void* stream);
 
+/* Diagnostic (no counterpart in the paper): the same check for the energy
+ * kernel's TMA staging (mixed spin).  One 16^3 tile of zeros with the kernel's
+ * test hook that issues no copy, so its first stage wait can only end by the
+ * limit `wait_cycles` (1000 .. 4e9); the kernel records code 7 and leaves with
+ * nothing in flight.  Returns LNO_OT_ETIMEOUT when the wait gave up as
+ * designed (*code = 7), LNO_OT_OK if it did not, another status on a CUDA
+ * failure or bad argument.  Allocates its own scratch; synchronous on
+ * `stream`. */
+LNO_OT_API int lno_ot_selftest_energy_timeout(int device, long long wait_cycles, int* code,
+                                              void* stream);
+
 /* The same product as lno_ot_selftest_gemm (same slicing, same kernel, same
  * result) for callers that must not allocate device memory: programs whose
  * HBM is owned by their own pool or arena, or code paths where a cudaMalloc

@@ -79,6 +79,10 @@ struct EnergyArgs {
   // persistent grid of at most (resident CTAs per SM) * nsm CTAs
   int nchunk, nitems, nsm;
   int* flag;           // device error flag (bounded waits of the TMA-staged variant)
+  // bounded-wait test hook of the TMA-staged variant: stage waits give up after
+  // wait_cycles (0: the normal 4e9); starve = 1 issues no copy at all
+  long long wait_cycles;
+  int starve;
   // Laplace form (Sec. 3.7, eq laplace_transform): with lap_w != 0 the
   // kernels weight each element by -lap_w exp(lap_s D) instead of 1/D (one
   // quadrature point of 1/D = -sum_q w_q exp(s_q D), D < 0)

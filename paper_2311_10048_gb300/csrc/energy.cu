@@ -604,6 +604,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
     }
   };
   auto issue = [&](int cg, int cq, int st) {
+    if (a.starve) return;   // test hook: nothing will complete the stage barrier
     const int3 bk = a.blocks[cq];
     const int a0 = bk.x * TB, b0 = bk.y * TB, c0 = bk.z * TB;
     const uint32_t bar = smem_u32(fullb + st);
@@ -629,7 +630,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
 #pragma unroll 1
     for (int st = 0; st < 2 && pw < a.nitems; ++st) {
       if (tid == 0) issue(pg, pq, st);
-      ++issued;
+      issued += a.starve ? 0 : 1;
       advance(pw, pg, pq);
     }
   }
@@ -639,7 +640,8 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
     const int a0 = blk.x * TB, b0 = blk.y * TB, c0 = blk.z * TB;
     if constexpr (TM) {   // this tile's sub-cubes
       const int st = (int)(it & 1u);
-      const bool ok = mbar_wait_bounded(smem_u32(fullb + st), (it >> 1) & 1u, 4000000000LL);
+      const bool ok = mbar_wait_bounded(smem_u32(fullb + st), (it >> 1) & 1u,
+                                        a.wait_cycles > 0 ? a.wait_cycles : 4000000000LL);
       if (__syncthreads_or(!ok)) {
         // give up: record the error, let the copies in flight land, leave
         if (tid == 0) {
@@ -852,7 +854,7 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
     if constexpr (TM) {   // stage it & 1 is free: the tile two ahead goes there
       if (pw < a.nitems) {
         if (tid == 0) issue(pg, pq, (int)(it & 1u));
-        ++issued;
+        issued += a.starve ? 0 : 1;
         advance(pw, pg, pq);
       }
       ++it;
@@ -1131,6 +1133,76 @@ cudaError_t launch_orbital_partition(const OrbPartArgs& A, cudaStream_t st) {
   if (A.na + A.nb <= 0) return cudaSuccess;
   orbital_partition<<<A.na + A.nb, 256, 0, st>>>(A);
   return cudaGetLastError();
+}
+
+// Bounded-wait check of the TMA-staged energy kernel: one mixed-spin 16^3
+// tile of zeros (two occupied, 16 virtual orbitals per spin) with the test hook
+// that issues no copy, so the first stage wait can only end by its limit.
+// *code gets the kernel's flag (7 when the wait gave up).
+cudaError_t energy_timeout_selftest(long long wait_cycles, int nsm, int* code, cudaStream_t st) {
+  constexpr int nv = 16, no = 2, pitch = 16;
+  const int64_t xs = (int64_t)nv * nv * pitch, zs = (int64_t)npairs(nv) * pitch;
+  const int64_t vts = 2LL * nv * pitch + (int64_t)nv * pitch;
+  const size_t bytes = (size_t)(xs + zs + vts) * 4 + 4 * (no + nv) * 8 + 2 * no * nv * 8 +
+                       8 * 8 + 64 + 4 * 256;
+  unsigned char* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), bytes, st);
+  if (e != cudaSuccess) return e;
+  auto finish = [&](cudaError_t r) {
+    cudaFreeAsync(buf, st);
+    return r;
+  };
+  if ((e = cudaMemsetAsync(buf, 0, bytes, st)) != cudaSuccess) return finish(e);
+  unsigned char* p = buf;
+  auto take = [&](size_t n) {
+    unsigned char* q = p;
+    p += (n + 255) / 256 * 256;
+    return q;
+  };
+  float* X = reinterpret_cast<float*>(take(xs * 4));
+  float* Z = reinterpret_cast<float*>(take(zs * 4));
+  float* VT = reinterpret_cast<float*>(take(vts * 4));
+  double* eps = reinterpret_cast<double*>(take(2 * (no + nv) * 8));
+  double* t1 = reinterpret_cast<double*>(take(2 * no * nv * 8));
+  double* part = reinterpret_cast<double*>(take(8 * 8));
+  int* flag = reinterpret_cast<int*>(take(64));
+  int3* blk = reinterpret_cast<int3*>(take(16));
+  Trip* trip = reinterpret_cast<Trip*>(take(16));
+  const int3 hb = make_int3(0, 0, 0);
+  const Trip ht{0, 1, 0};
+  if ((e = cudaMemcpyAsync(blk, &hb, sizeof hb, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(trip, &ht, sizeof ht, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return finish(e);
+  EnergyArgs a{};
+  a.kind = MIXED;
+  a.nvs = a.nvt = nv;
+  a.nos = a.not_ = no;
+  a.eps_s = eps;
+  a.eps_t = eps + no + nv;
+  a.t1s = t1;
+  a.t1t = t1 + no * nv;
+  a.blocks = blk;
+  a.nblocks = 1;
+  a.pitch_x = a.pitch_z = pitch;
+  a.x_stride = xs;
+  a.z_stride = zs;
+  a.trips = trip;
+  a.partial = part;
+  a.nsm = nsm;
+  a.flag = flag;
+  a.wait_cycles = wait_cycles;
+  a.starve = 1;
+  CUtensorMap mx, mz;
+  if (cube_maps(a, X, Z, 1, &mx, &mz) != LNO_OT_OK) return finish(cudaErrorInvalidValue);
+  launch_ef32<true, false, false, false, true>(a, X, Z, VT, vts, pitch, pitch, 0, 1, 1, mx, mz,
+                                               st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return finish(e);
+  int h = 0;
+  if ((e = cudaMemcpyAsync(&h, flag, sizeof h, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return finish(e);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return finish(e);
+  *code = h;
+  return finish(cudaSuccess);
 }
 
 cudaError_t launch_neumaier_sum(const double* e, int64_t n, double* out, cudaStream_t st) {

@@ -44,6 +44,7 @@ cudaError_t launch_reduce_partials(const double* partial, int np, const double* 
                                    int ntrip, double* e_trip, cudaStream_t st);
 cudaError_t launch_orbital_partition(const OrbPartArgs& A, cudaStream_t st);
 cudaError_t launch_neumaier_sum(const double* e, int64_t n, double* out, cudaStream_t st);
+cudaError_t energy_timeout_selftest(long long wait_cycles, int nsm, int* code, cudaStream_t st);
 // pack.cu
 template <class St>
 cudaError_t launch_transpose_block(const double*, int, int, int, int, int, int, int, St,
@@ -2642,6 +2643,20 @@ int lno_ot_selftest_timeout(int device, long long wait_cycles, int* code, void* 
   CU(cudaStreamSynchronize(st));
   if (code) *code = hflag;
   return hflag ? LNO_OT_ETIMEOUT : LNO_OT_OK;
+}
+
+int lno_ot_selftest_energy_timeout(int device, long long wait_cycles, int* code, void* stream) {
+  if (wait_cycles < 1000 || wait_cycles > tc_default_wait_cycles()) return LNO_OT_EINVAL;
+  if (code) *code = 0;
+  CU(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  CU(cudaGetDeviceProperties(&prop, device));
+  if (!(prop.major == 10 && prop.minor == 3)) return LNO_OT_EUNSUPPORTED;
+  int h = 0;
+  CU(energy_timeout_selftest(wait_cycles, prop.multiProcessorCount, &h,
+                             static_cast<cudaStream_t>(stream)));
+  if (code) *code = h;
+  return h ? LNO_OT_ETIMEOUT : LNO_OT_OK;
 }
 
 const char* lno_ot_last_error(void) { return g_last_error.c_str(); }

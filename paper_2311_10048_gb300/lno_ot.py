@@ -118,6 +118,9 @@ def load_library(build_if_missing=False):
     lib.lno_ot_selftest_timeout.argtypes = [C.c_int, C.c_longlong, C.POINTER(C.c_int),
                                             C.c_void_p]
     lib.lno_ot_selftest_timeout.restype = C.c_int
+    lib.lno_ot_selftest_energy_timeout.argtypes = [C.c_int, C.c_longlong, C.POINTER(C.c_int),
+                                                   C.c_void_p]
+    lib.lno_ot_selftest_energy_timeout.restype = C.c_int
     _lib = lib
     return lib
 

@@ -1,11 +1,13 @@
-"""Bounded device waits of the contraction kernel, exercised without a fault.
+"""Bounded device waits of the contraction and energy kernels, exercised
+without a fault.
 
-lno_ot_selftest_timeout runs one tile with the kernel's test hook that issues
-no copy, so the MMA thread's first wait for operand data can only end by its
-time limit (a flag that nothing sets).  The call must come back with
-LNO_OT_ETIMEOUT and the code of a wait for work, twice in a row, and the
+lno_ot_selftest_timeout runs one tile with the contraction kernel's test hook
+that issues no copy, so the MMA thread's first wait for operand data can only
+end by its time limit (a flag that nothing sets).  The call must come back
+with LNO_OT_ETIMEOUT and the code of a wait for work, twice in a row, and the
 device must then still compute the small domain c0 correctly (stored oracle
-values) and a plain product on the same kernel.
+values) and a plain product on the same kernel.  lno_ot_selftest_energy_timeout
+does the same for the TMA staging of the energy kernel (code 7).
 """
 import ctypes
 import json
@@ -52,3 +54,21 @@ def test_bounded_wait_gives_up_and_device_recovers(lib):
     assert rc == 0
     ref = B @ A.T
     assert np.abs(dC.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-8
+
+
+def test_energy_stage_wait_gives_up_and_device_recovers(lib):
+    lno_ot.load_library()
+    for _ in range(2):
+        code = ctypes.c_int(-1)
+        rc = lib.lno_ot_selftest_energy_timeout(0, 2_000_000, ctypes.byref(code), None)
+        assert rc == lno_ot.ETIMEOUT, lib.lno_ot_strerror(rc)
+        assert code.value == 7, code.value
+    assert lib.lno_ot_selftest_energy_timeout(0, 10, None, None) == lno_ot.EINVAL
+
+    g = json.load(open(os.path.join(GOLD, "c0_energy.json")))
+    dd = lno_ot.to_device(config_domain("c0"))
+    ctx = lno_ot.Context(0, "bf16x10")
+    out = ctx.energy(dd)
+    ctx.close()
+    for c in CASES:
+        assert abs(out[c] - g["cases"][c]["sum"]) <= 1e-8, c
