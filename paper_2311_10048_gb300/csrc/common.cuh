@@ -83,6 +83,9 @@ struct EnergyArgs {
   // wait_cycles (0: the normal 4e9); starve = 1 issues no copy at all
   long long wait_cycles;
   int starve;
+  // mixed spin: Y and Z' stored as 16^3 tiles (kOutYTile / kOutZTile, strides
+  // in floats per triplet above); selects the TMA-staged kernel
+  int tiled;
   // Laplace form (Sec. 3.7, eq laplace_transform): with lap_w != 0 the
   // kernels weight each element by -lap_w exp(lap_s D) instead of 1/D (one
   // quadrature point of 1/D = -sum_q w_q exp(s_q D), D < 0)
@@ -145,12 +148,36 @@ struct TcProb {
   void* out;        // output of this problem: [N][ldo] (transposed) or [M][ldo] (row-major)
 };
 
+// Output layout of a row-major (RM) float32 contraction launch.
+//   kOutRows:  out[m][n], pitch ldo.
+//   kOutYTile: mixed-spin Y, rows m = b nvt + C, columns a, stored as 16^3
+//              tiles (b/16, C/16, a/16), tile index (B nbt + C') nbs + A; in a
+//              tile, row r = (b%16) 16 + C%16 holds 16 floats of a with its four
+//              16-byte chunks permuted (chunk ^ ((r >> 1) & 3)).
+//   kOutZTile: mixed-spin Z', rows m = pair(a, b) (a < b), columns C, stored as
+//              tiles (a/16 <= b/16, C/16), tile index (B(B+1)/2 + A) nbt + C';
+//              row r = (a%16) 16 + b%16 sits at row r ^ ((r >> 1) & 1) of the
+//              tile.
+// The energy kernel reads each 16^3 sub-cube of the tiled layouts with one
+// 16 KB bulk copy, in the shared-memory layout its element loops index.
+constexpr int kOutRows = 0, kOutYTile = 1, kOutZTile = 2;
+struct TcOut {
+  int mode;
+  int nvt;    // kOutYTile: C count per b
+  int nbs;    // 16-blocks of a (and b)
+  int nbt;    // 16-blocks of C
+};
+constexpr int kTile = 4096;   // floats of one 16^3 tile
+
 // Bounded-wait settings of one contraction launch: wait_cycles limits every
 // wait for work; starve = 1 is the timeout test hook (no copy is issued, so
 // the first wait for data runs out).  Library calls use tc_normal().
 struct TcDiag {
   long long wait_cycles;
   int starve;
+  // mixed spin: Y and Z' stored as 16^3 tiles (kOutYTile / kOutZTile, strides
+  // in floats per triplet above); selects the TMA-staged kernel
+  int tiled;
 };
 
 // tc_gemm.cu: grouped sliced contraction.  mA: maps with 128-row boxes,
@@ -159,13 +186,12 @@ struct TcDiag {
 template <int S, int BN, typename OutT, bool TF = false, bool RM = false>
 cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
                            int nprob, int M, int N, int ldo, double scale, int* flag,
-                           unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag);
+                           unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag,
+                           TcOut lay = TcOut{kOutRows, 0, 0, 0});
 long long tc_default_wait_cycles();
 inline TcDiag tc_normal() { return TcDiag{tc_default_wait_cycles(), 0}; }
 int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int S,
                      int64_t slice_stride, int box_rows, int esz = 2);
-int make_f32_map(CUtensorMap* map, const void* base, int rank, const int64_t* dims,
-                 const int64_t* strides, const int* box, bool sw64);
 int sliced_product_bn(int S);
 cudaError_t launch_sliced_product(int S, const CUtensorMap* mA, const CUtensorMap* mB,
                                   const TcProb* dp, int M, int N, double scale, int* flag,

@@ -397,21 +397,19 @@ __device__ __forceinline__ float lap_factor(float shi, float slo, float D) {
 // FU (mixed spin only): V = V(T1) + V(f_ov) in one pass; the f_ov planes sit
 // vt_half floats after the T1 planes of each triplet's table and the f_ov
 // coefficients come from a.fs / a.ft.
-// TM (mixed spin only): the three sub-cubes come by TMA into a two-stage ring
-// in dynamic shared memory (tile i in stage i & 1, issued two tiles ahead by
-// thread 0, completion on one mbarrier per stage) instead of through
-// registers:
-//   T1[b][c][a]  one 16x16x16 box of the 4-D map (a, c, b, triplet) over Y,
-//                64-byte rows with the 64-byte swizzle (16-byte chunk
-//                index XOR (row >> 1) & 3)
-//   T2[a][c][b]  the same map at (b0, c0, a0)
-//   T3[b][a][C]  16 boxes of 16 rows of the 3-D map (C, pair row, triplet)
-//                over Z', one per b (rows (a0..a0+15, b) are consecutive)
+// TM (mixed spin only): Y and Z' are stored as 16^3 tiles (kOutYTile /
+// kOutZTile), and the three sub-cubes come by bulk copies (16 KB each) into a
+// two-stage ring in dynamic shared memory (tile i in stage i & 1, issued two
+// tiles ahead by thread 0, completion on one mbarrier per stage) instead of
+// through registers:
+//   T1[b][c][a]  Y tile (B, C, A), 64-byte rows, 16-byte chunk q of row r at
+//                chunk q ^ ((r >> 1) & 3)
+//   T2[a][c][b]  Y tile (A, C, B), the same row layout
+//   T3[a][b][C]  Z' tile (A, B, C), row r = a 16 + b at row r ^ ((r >> 1) & 1)
 template <bool MIXED, bool FM, bool FU, bool LAP, bool TM>
 __global__ void __launch_bounds__(256, 2)
 energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ Z,
-           const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt, int64_t vt_half,
-           const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapZ) {
+           const float* __restrict__ VT, int64_t vt_stride, int pv, int pvt, int64_t vt_half) {
   static_assert(!FU || (MIXED && !FM), "the fused f_ov pass is the mixed-spin W (W + V) sum");
   static_assert(!TM || (MIXED && !FU), "TMA staging: mixed spin without the fused f_ov pass");
   constexpr int P1 = 20, P2 = 18, P3 = 24;
@@ -606,16 +604,18 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
   auto issue = [&](int cg, int cq, int st) {
     if (a.starve) return;   // test hook: nothing will complete the stage barrier
     const int3 bk = a.blocks[cq];
-    const int a0 = bk.x * TB, b0 = bk.y * TB, c0 = bk.z * TB;
+    const int nbs = (nvs + TB - 1) / TB, nbt = (nvt + TB - 1) / TB;
+    const float* Yg = X + (int64_t)cg * a.x_stride;
+    const float* Zt = Z + (int64_t)cg * a.z_stride;
     const uint32_t bar = smem_u32(fullb + st);
     float* base = ring + 3 * CUBE * st;
     mbar_expect_tx(bar, 3u * CUBE * 4u);
-    tma_load_4d(smem_u32(base), &mapX, bar, a0, c0, b0, cg);
-    tma_load_4d(smem_u32(base + CUBE), &mapX, bar, b0, c0, a0, cg);
-#pragma unroll 1
-    for (int bl = 0; bl < TB; ++bl)
-      tma_load_3d(smem_u32(base + 2 * CUBE + bl * TB * TB), &mapZ, bar, c0,
-                  (int)pair_index(a0, b0 + bl), cg);
+    bulk_load(smem_u32(base), Yg + ((int64_t)(bk.y * nbt + bk.z) * nbs + bk.x) * CUBE,
+              CUBE * 4u, bar);
+    bulk_load(smem_u32(base + CUBE), Yg + ((int64_t)(bk.x * nbt + bk.z) * nbs + bk.y) * CUBE,
+              CUBE * 4u, bar);
+    bulk_load(smem_u32(base + 2 * CUBE),
+              Zt + ((int64_t)(bk.y * (bk.y + 1) / 2 + bk.x) * nbt + bk.z) * CUBE, CUBE * 4u, bar);
   };
   int pw = w, pg = g, pq = q, issued = 0;
   uint32_t it = 0;   // tiles of this CTA so far
@@ -782,7 +782,8 @@ energy_f32(EnergyArgs a, const float* __restrict__ X, const float* __restrict__ 
             for (int sb = 0; sb < 2; ++sb) {
               const int bl = bl0 + sb;
               const bool valid = rowok[sb] && a0 + al < b0 + bl;
-              const float x3 = TM ? cur[2 * CUBE + (bl * TB + al) * TB + cl]
+              const int r3 = al * TB + bl;
+              const float x3 = TM ? cur[2 * CUBE + (r3 ^ ((r3 >> 1) & 1)) * TB + cl]
                                   : T3[(al * TB + bl) * P3 + cl];
               const float vab = kab[al][bl].x;
               const float w = x1a[sb][u] - x2a[sb] + x3;
@@ -1007,28 +1008,12 @@ int ef32_resident() {
 template <bool M, bool F, bool U, bool L, bool T>
 void launch_ef32(EnergyArgs a, const float* X, const float* Z, const float* vtab,
                  int64_t vt_stride, int pv, int pvt, int64_t vt_half, int ntrip, int nchunks,
-                 const CUtensorMap& mx, const CUtensorMap& mz, cudaStream_t st) {
+                 cudaStream_t st) {
   a.nchunk = nchunks;
   a.nitems = ntrip * nchunks;
   const int grid = std::max(1, std::min(a.nitems, ef32_resident<M, F, U, L, T>() * a.nsm));
   energy_f32<M, F, U, L, T><<<grid, 256, T ? kRingBytes : 0, st>>>(a, X, Z, vtab, vt_stride, pv,
-                                                                   pvt, vt_half, mx, mz);
-}
-
-// Tensor maps of the TMA-staged mixed variant over one group's Y (rows b nvt
-// + C, pitch pitch_x) and Z' (rows pair(a, b), pitch pitch_z).
-int cube_maps(const EnergyArgs& a, const float* X, const float* Z, int ntrip, CUtensorMap* mx,
-              CUtensorMap* mz) {
-  const int64_t dx[4] = {a.pitch_x, a.nvt, a.nvs, ntrip};
-  const int64_t sx[3] = {(int64_t)a.pitch_x * 4, (int64_t)a.nvt * a.pitch_x * 4, a.x_stride * 4};
-  const int bx[4] = {TB, TB, TB, 1};
-  const int64_t nrow = a.pitch_z > 0 ? a.z_stride / a.pitch_z : 0;
-  const int64_t dz[3] = {a.pitch_z, std::max<int64_t>(nrow, 1), ntrip};
-  const int64_t sz[2] = {(int64_t)a.pitch_z * 4, a.z_stride * 4};
-  const int bz[3] = {TB, TB, 1};
-  int rc = make_f32_map(mx, X, 4, dx, sx, bx, true);
-  if (rc == LNO_OT_OK) rc = make_f32_map(mz, Z, 3, dz, sz, bz, false);
-  return rc;
+                                                                   pvt, vt_half);
 }
 
 // float32-X path: V-table prep + energy (nchunks items per triplet on a
@@ -1040,10 +1025,8 @@ cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* 
   if (nchunks < 1 || nchunks > a.nblocks || a.nsm < 1) return cudaErrorInvalidValue;
   dim3 gp(64, ntrip);
   energy_prep<<<gp, 256, 0, st>>>(a, vtab, vt_stride, pv, pvt);
-  static const CUtensorMap none{};
 #define LNO_EF32(M, F, L) \
-  launch_ef32<M, F, false, L, false>(a, X, Z, vtab, vt_stride, pv, pvt, 0, ntrip, nchunks, none, \
-                                     none, st)
+  launch_ef32<M, F, false, L, false>(a, X, Z, vtab, vt_stride, pv, pvt, 0, ntrip, nchunks, st)
   const bool lap = a.lap_w != 0.0;
   if (a.kind == SAME) {
     if (a.vmode) {
@@ -1053,17 +1036,19 @@ cudaError_t launch_energy_f32(const EnergyArgs& a, const float* X, const float* 
     }
   } else if (a.vmode) {
     if (lap) LNO_EF32(true, true, true); else LNO_EF32(true, true, false);
+  } else if (!a.tiled) {
+    if (lap) LNO_EF32(true, false, true); else LNO_EF32(true, false, false);
   } else {
-    // mixed spin: sub-cubes staged by TMA
-    if (a.flag == nullptr || a.pitch_x % 16 || a.pitch_z % 16) return cudaErrorInvalidValue;
-    CUtensorMap mx, mz;
-    if (cube_maps(a, X, Z, ntrip, &mx, &mz) != LNO_OT_OK) return cudaErrorInvalidValue;
+    // mixed spin, tiled Y / Z': sub-cubes staged by bulk copies
+    if (a.flag == nullptr || (reinterpret_cast<uintptr_t>(X) & 15) ||
+        (reinterpret_cast<uintptr_t>(Z) & 15))
+      return cudaErrorInvalidValue;
     if (lap)
       launch_ef32<true, false, false, true, true>(a, X, Z, vtab, vt_stride, pv, pvt, 0, ntrip,
-                                                  nchunks, mx, mz, st);
+                                                  nchunks, st);
     else
       launch_ef32<true, false, false, false, true>(a, X, Z, vtab, vt_stride, pv, pvt, 0, ntrip,
-                                                   nchunks, mx, mz, st);
+                                                   nchunks, st);
   }
 #undef LNO_EF32
   return cudaGetLastError();
@@ -1094,13 +1079,13 @@ cudaError_t launch_energy_f32_fused(const EnergyArgs& a, const float* X, const f
   a1.vmode = 1;
   energy_prep<<<gp, 256, 0, st>>>(a0, vtab, 2 * vt_half, pv, pvt);
   energy_prep<<<gp, 256, 0, st>>>(a1, vtab + vt_half, 2 * vt_half, pv, pvt);
-  static const CUtensorMap none{};
+  if (a.tiled) return cudaErrorInvalidValue;   // the fused f_ov pass reads [pair][a] rows
   if (a.lap_w != 0.0)
     launch_ef32<true, false, true, true, false>(a0, X, Z, vtab, 2 * vt_half, pv, pvt, vt_half,
-                                                ntrip, nchunks, none, none, st);
+                                                ntrip, nchunks, st);
   else
     launch_ef32<true, false, true, false, false>(a0, X, Z, vtab, 2 * vt_half, pv, pvt, vt_half,
-                                                 ntrip, nchunks, none, none, st);
+                                                 ntrip, nchunks, st);
   return cudaGetLastError();
 }
 
@@ -1141,7 +1126,7 @@ cudaError_t launch_orbital_partition(const OrbPartArgs& A, cudaStream_t st) {
 // *code gets the kernel's flag (7 when the wait gave up).
 cudaError_t energy_timeout_selftest(long long wait_cycles, int nsm, int* code, cudaStream_t st) {
   constexpr int nv = 16, no = 2, pitch = 16;
-  const int64_t xs = (int64_t)nv * nv * pitch, zs = (int64_t)npairs(nv) * pitch;
+  const int64_t xs = kTile, zs = kTile;   // one Y tile and one Z' tile
   const int64_t vts = 2LL * nv * pitch + (int64_t)nv * pitch;
   const size_t bytes = (size_t)(xs + zs + vts) * 4 + 4 * (no + nv) * 8 + 2 * no * nv * 8 +
                        8 * 8 + 64 + 4 * 256;
@@ -1192,10 +1177,8 @@ cudaError_t energy_timeout_selftest(long long wait_cycles, int nsm, int* code, c
   a.flag = flag;
   a.wait_cycles = wait_cycles;
   a.starve = 1;
-  CUtensorMap mx, mz;
-  if (cube_maps(a, X, Z, 1, &mx, &mz) != LNO_OT_OK) return finish(cudaErrorInvalidValue);
-  launch_ef32<true, false, false, false, true>(a, X, Z, VT, vts, pitch, pitch, 0, 1, 1, mx, mz,
-                                               st);
+  a.tiled = 1;
+  launch_ef32<true, false, false, false, true>(a, X, Z, VT, vts, pitch, pitch, 0, 1, 1, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return finish(e);
   int h = 0;
   if ((e = cudaMemcpyAsync(&h, flag, sizeof h, cudaMemcpyDeviceToHost, st)) != cudaSuccess)

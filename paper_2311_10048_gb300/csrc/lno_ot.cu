@@ -280,7 +280,7 @@ const CUtensorMap& map_for(const Operand& op, int box) {
 cudaError_t launch_contract(int S, bool tf, int bn_req, const Operand& A0, const Operand& A1,
                             const Operand& B0, const Operand& B1, const TcProb* dpt, int nprob,
                             int M, int N, int ldo, double scale, int* flag, int nsm,
-                            cudaStream_t st) {
+                            cudaStream_t st, TcOut lay) {
   const int bn = contract_bn(S, bn_req);
   CUtensorMap mA[2] = {B0.map128, B1.map128};
   CUtensorMap mB[2] = {map_for(A0, bn), map_for(A1, bn)};
@@ -288,13 +288,13 @@ cudaError_t launch_contract(int S, bool tf, int bn_req, const Operand& A0, const
   std::swap(M, N);
 #define LNO_CALL(SS, BB)                                                                      \
   launch_tc_gemm<SS, BB, float, false, true>(mA, mB, dpt, nprob, M, N, ldo, scale, flag, nullptr, \
-                                             nsm, st, dg)
+                                             nsm, st, dg, lay)
   if (tf)
     return bn == 128
                ? launch_tc_gemm<2, 128, float, true, true>(mA, mB, dpt, nprob, M, N, ldo, scale,
-                                                           flag, nullptr, nsm, st, dg)
+                                                           flag, nullptr, nsm, st, dg, lay)
                : launch_tc_gemm<2, 256, float, true, true>(mA, mB, dpt, nprob, M, N, ldo, scale,
-                                                           flag, nullptr, nsm, st, dg);
+                                                           flag, nullptr, nsm, st, dg, lay);
   if (S == 2) return bn == 128 ? LNO_CALL(2, 128) : LNO_CALL(2, 256);
   if (S == 3) return bn == 64 ? LNO_CALL(3, 64) : LNO_CALL(3, 128);
   if (S == 4) return bn == 64 ? LNO_CALL(4, 64) : bn == 96 ? LNO_CALL(4, 96) : LNO_CALL(4, 128);
@@ -881,7 +881,8 @@ struct SpinPass {
   // ---- contraction launches -------------------------------------------------
   int contract(int nprob, int M, int N, int ldo, const Operand& opA0, const Operand& opA1,
                const Operand& opB0, const Operand& opB1, const std::vector<ProbF64>& pf,
-               const std::vector<TcProb>& pt, ProbF64* dpf, TcProb* dpt) {
+               const std::vector<TcProb>& pt, ProbF64* dpf, TcProb* dpt,
+               TcOut lay = TcOut{kOutRows, 0, 0, 0}) {
     cudaEvent_t e0 = R.event(), e1 = R.event();
     if (e0) cudaEventRecord(e0, R.st);
     if (R.f64) {
@@ -891,7 +892,7 @@ struct SpinPass {
       CU(cudaMemcpyAsync(dpt, pt.data(), nprob * sizeof(TcProb), cudaMemcpyHostToDevice, R.st));
       const double scale = R.sigT * R.sigI * std::ldexp(1.0, R.tf32 ? -20 : -14);
       CU(launch_contract(R.S, R.tf32, bn, opA0, opA1, opB0, opB1, dpt, nprob, M, N, ldo, scale,
-                         R.ctx->d_flag, R.ctx->nsm, R.st));
+                         R.ctx->d_flag, R.ctx->nsm, R.st, lay));
     }
     if (e1) cudaEventRecord(e1, R.st);
     if (e0 && e1) R.contract_ev.push_back({e0, e1});
@@ -924,7 +925,17 @@ struct SpinPass {
     const int M2 = vt;                                      // mixed Z': rows C
     const int64_t N2 = is_mixed ? npairs(v) : 0;
     const int P2 = (int)round_up(std::max(M2, 1), 16);
-    const int64_t per_trip = (N1 * P1 + N2 * P2) * (int64_t)esz;
+    const int nbs = (v + 15) / 16, nbt = (vt + 15) / 16;
+    // mixed spin on the tensor cores without f_ov: Y and Z' as 16^3 tiles (the
+    // TMA-staged energy kernel reads each sub-cube with one bulk copy);
+    // otherwise rows [pair][a] of pitch P1 (P2)
+    const bool fov = R.fov[0] != nullptr;   // restricted open-shell f_ov term
+    const bool tiled = !f64 && is_mixed && !fov;
+    const int64_t xs = tiled ? (int64_t)nbs * nbt * nbs * kTile : N1 * P1;   // per triplet
+    const int64_t zs = tiled ? (int64_t)nbs * (nbs + 1) / 2 * nbt * kTile : N2 * P2;
+    const TcOut lay1 = tiled ? TcOut{kOutYTile, vt, nbs, nbt} : TcOut{kOutRows, 0, 0, 0};
+    const TcOut lay2 = tiled ? TcOut{kOutZTile, 0, nbs, nbt} : TcOut{kOutRows, 0, 0, 0};
+    const int64_t per_trip = (xs + zs) * (int64_t)esz;
     const int64_t budget = (int64_t)6 << 30;
     bn = 0;
     group_cap = 64;
@@ -940,13 +951,12 @@ struct SpinPass {
     const int Gshape = G;
     G = std::min(G, ntrip);
     char *X = nullptr, *Z = nullptr;
-    TRY(A.get(&X, (size_t)(G * N1 * P1 * esz) + 64));
-    if (is_mixed) TRY(A.get(&Z, (size_t)(G * N2 * P2 * esz) + 64));
-    CU(cudaMemsetAsync(X, 0, (size_t)(G * N1 * P1 * esz), R.st));
-    if (is_mixed) CU(cudaMemsetAsync(Z, 0, (size_t)(G * N2 * P2 * esz), R.st));
+    TRY(A.get(&X, (size_t)(G * xs * esz) + 64));
+    if (is_mixed) TRY(A.get(&Z, (size_t)(G * zs * esz) + 64));
+    CU(cudaMemsetAsync(X, 0, (size_t)(G * xs * esz), R.st));
+    if (is_mixed) CU(cudaMemsetAsync(Z, 0, (size_t)(G * zs * esz), R.st));
     // cube tiles
     std::vector<int3> blocks;
-    const int nbs = (v + 15) / 16, nbt = (vt + 15) / 16;
     if (!is_mixed) {
       for (int a = 0; a < nbs; ++a)
         for (int b = a; b < nbs; ++b)
@@ -976,7 +986,6 @@ struct SpinPass {
                       : std::max(1, std::min((int)blocks.size(),
                                              (64 * R.ctx->nsm + Gshape - 1) / Gshape));
     const int npart = f64 ? P : 8 * P;   // partials per triplet
-    const bool fov = R.fov[0] != nullptr;   // restricted open-shell f_ov term
     double* partial;
     TRY(A.get(&partial, (size_t)G * npart * (fov ? 2 : 1)));
     // float32 V tables of the tensor-core path, per triplet
@@ -1014,8 +1023,9 @@ struct SpinPass {
     ea.nblocks = (int)blocks.size();
     ea.pitch_x = P1;
     ea.pitch_z = P2;
-    ea.x_stride = N1 * P1;
-    ea.z_stride = N2 * P2;
+    ea.x_stride = xs;
+    ea.z_stride = zs;
+    ea.tiled = tiled ? 1 : 0;
     ea.lap_s = R.lap_s;
     ea.lap_w = R.lap_w;
     ea.nsm = R.ctx->nsm;
@@ -1044,7 +1054,7 @@ struct SpinPass {
       for (int g = 0; g < ng; ++g) {
         const Trip tr = cs.trips[g0 + g];
         const int i = tr.i, j = tr.j, k = tr.k;
-        char* Xg = X + (size_t)g * N1 * P1 * esz;
+        char* Xg = X + (size_t)g * xs * esz;
         if (!is_mixed) {
           const int64_t r_jk = (int64_t)slotAT[(size_t)j * o + k] * v;
           const int64_t r_ki = (int64_t)slotAT[(size_t)k * o + i] * v;
@@ -1076,7 +1086,7 @@ struct SpinPass {
           const int64_t a2_jK = (int64_t)slotAT2[(size_t)j * ot + K] * vt;
           const int64_t a2_iK = (int64_t)slotAT2[(size_t)i * ot + K] * vt;
           const int64_t bt_i = slotBT[i] * npairs(v), bt_j = slotBT[j] * npairs(v);
-          char* Zg = Z + (size_t)g * N2 * P2 * esz;
+          char* Zg = Z + (size_t)g * zs * esz;
           if (f64) {
             ProbF64& p = pf[g];
             p.nseg = 3;
@@ -1107,7 +1117,7 @@ struct SpinPass {
       if (!is_mixed) {
         TRY(contract(ng, M1, (int)N1, P1, AT, AT, BT, BT, pf, pt, dpf, dpt));
       } else {
-        TRY(contract(ng, M1, (int)N1, P1, A1, AT, BG, BF, pf, pt, dpf, dpt));
+        TRY(contract(ng, M1, (int)N1, P1, A1, AT, BG, BF, pf, pt, dpf, dpt, lay1));
         ProbF64* dpf2 = nullptr;
         TcProb* dpt2 = nullptr;
         // second problem list uses its own device array (the first may still be read)
@@ -1116,7 +1126,7 @@ struct SpinPass {
         } else {
           TRY(A.get(&dpt2, (size_t)ng));
         }
-        TRY(contract(ng, M2, (int)N2, P2, AT2, AT2, BT, BT, pf2, pt2, dpf2, dpt2));
+        TRY(contract(ng, M2, (int)N2, P2, AT2, AT2, BT, BT, pf2, pt2, dpf2, dpt2, lay2));
         A.drop(f64 ? (void*)dpf2 : (void*)dpt2);
       }
       // energy

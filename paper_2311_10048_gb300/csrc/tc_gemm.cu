@@ -204,6 +204,43 @@ __device__ __forceinline__ void store_row16(float* p, const uint32_t (&v)[16], i
   }
 }
 
+// One 16-float row chunk (columns n0 .. n0+15 of output row m) of a
+// row-major launch, in the launch's output layout; `left` = columns remaining
+// in the row (only those are written).
+__device__ __forceinline__ void store_out16(float* out, const TcOut& lay, int ldo, int m, int n0,
+                                            const uint32_t (&v)[16], int left) {
+  if (lay.mode == kOutRows) {
+    store_row16(out + (int64_t)m * ldo + n0, v, left);
+  } else if (lay.mode == kOutYTile) {
+    const int b = m / lay.nvt, c = m - b * lay.nvt;
+    const int r = ((b & 15) << 4) | (c & 15), sw = (r >> 1) & 3;
+    float* row = out + ((int64_t)((b >> 4) * lay.nbt + (c >> 4)) * lay.nbs + (n0 >> 4)) * kTile +
+                 r * 16;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float* d = row + ((q ^ sw) << 2);
+      if (left >= 4 * q + 4) {
+        *reinterpret_cast<float4*>(d) =
+            make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                        __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j < left) d[j] = __uint_as_float(v[4 * q + j]);
+      }
+    }
+  } else {   // kOutZTile: m = pair(a, b) = b (b - 1) / 2 + a
+    int b = (int)((1.0 + sqrt(1.0 + 8.0 * (double)m)) * 0.5);
+    while ((int64_t)b * (b - 1) / 2 > m) --b;
+    while ((int64_t)(b + 1) * b / 2 <= m) ++b;
+    const int a = m - (int)((int64_t)b * (b - 1) / 2);
+    const int A = a >> 4, B = b >> 4;
+    const int r = ((a & 15) << 4) | (b & 15), slot = r ^ ((r >> 1) & 1);
+    store_row16(out + ((int64_t)(B * (B + 1) / 2 + A) * lay.nbt + (n0 >> 4)) * kTile + slot * 16,
+                v, left);
+  }
+}
+
 template <int S, int BN>
 struct Cfg {
   static constexpr int kABytes = BM * BK * 2;          // one slice of A
@@ -232,7 +269,8 @@ __global__ void __launch_bounds__(192, 1)
 tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
                const TcProb* __restrict__ probs, int nprob, int M, int N, int ldo, double scale,
-               int* __restrict__ flag, unsigned long long* __restrict__ amax, TcDiag diag) {
+               int* __restrict__ flag, unsigned long long* __restrict__ amax, TcDiag diag,
+               TcOut lay) {
   using C = Cfg<S, BN>;
   constexpr int BKE = TF ? BK / 2 : BK;   // elements per 64-byte row
   constexpr int KM = TF ? 8 : 16;         // K of one MMA
@@ -449,7 +487,7 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
           tmem_ld_wait();
           const int n0 = nt * BN + c * 16;
           if constexpr (RM) {
-            if (mok) store_row16(reinterpret_cast<float*>(out) + (int64_t)m * ldo + n0, v, N - n0);
+            if (mok) store_out16(reinterpret_cast<float*>(out), lay, ldo, m, n0, v, N - n0);
           } else {
             OutT* op = out + (int64_t)n0 * ldo + m;
 #pragma unroll
@@ -486,14 +524,14 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
         tc_fence_before();
         mbar_arrive(tempty);
         if (mok) {
-          float* orow = reinterpret_cast<float*>(out) + (int64_t)m * ldo + nt * BN;
 #pragma unroll
           for (int c = 0; c < BN / 16; ++c) {
             if (c < nch) {
               uint32_t w[16];
 #pragma unroll
               for (int j = 0; j < 16; ++j) w[j] = v[c * 16 + j];
-              store_row16(orow + c * 16, w, N - nt * BN - c * 16);
+              const int n0 = nt * BN + c * 16;
+              store_out16(reinterpret_cast<float*>(out), lay, ldo, m, n0, w, N - n0);
             }
           }
         }
@@ -516,7 +554,7 @@ tc_gemm_sliced(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
               for (int g = S - 1; g >= 1; --g) lo = __fadd_rn(lo, __uint_as_float(acc[g][j]));
               v[j] = __float_as_uint(__fmul_rn(__fadd_rn(__uint_as_float(acc[0][j]), lo), fscale));
             }
-            if (mok) store_row16(reinterpret_cast<float*>(out) + (int64_t)m * ldo + n0, v, N - n0);
+            if (mok) store_out16(reinterpret_cast<float*>(out), lay, ldo, m, n0, v, N - n0);
             continue;
           }
           OutT* op = out + (int64_t)n0 * ldo + m;
@@ -610,52 +648,26 @@ int make_operand_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t row
   return r == CUDA_SUCCESS ? LNO_OT_OK : LNO_OT_ECUDA;
 }
 
-// Tiled map over float32 data of rank 3..5: dims innermost first, byte strides
-// of dims 1.., box extents; 64-byte swizzle when sw64 (box rows of 64 bytes),
-// zero fill beyond the dims.  No L2 promotion: the boxes' 64-byte rows lie 1-2
-// KB apart, and a promoted 256-byte fetch would bring in columns that other
-// tiles use much later.
-int make_f32_map(CUtensorMap* map, const void* base, int rank, const int64_t* dims,
-                 const int64_t* strides, const int* box, bool sw64) {
-  EncodeTiledFn enc = get_encode();
-  if (!enc) return LNO_OT_ECUDA;
-  if (rank < 3 || rank > 5 || (reinterpret_cast<uintptr_t>(base) & 15) || (box[0] * 4) % 16 ||
-      (sw64 && box[0] * 4 != 64))
-    return LNO_OT_EINVAL;
-  cuuint64_t d[5], st[4];
-  cuuint32_t bx[5], es[5];
-  for (int i = 0; i < rank; ++i) {
-    if (dims[i] < 1 || box[i] < 1 || box[i] > 256) return LNO_OT_EINVAL;
-    d[i] = (cuuint64_t)dims[i];
-    bx[i] = (cuuint32_t)box[i];
-    es[i] = 1;
-    if (i > 0) {
-      if (strides[i - 1] % 16) return LNO_OT_EINVAL;
-      st[i - 1] = (cuuint64_t)strides[i - 1];
-    }
-  }
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base),
-                   d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? LNO_OT_OK : LNO_OT_ECUDA;
-}
-
 // mB must be maps with boxes of BN rows; mA boxes of 128 rows.
 template <int S, int BN, typename OutT, bool TF, bool RM>
 cudaError_t launch_tc_gemm(const CUtensorMap* mA, const CUtensorMap* mB, const TcProb* probs_dev,
                            int nprob, int M, int N, int ldo, double scale, int* flag,
-                           unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag) {
+                           unsigned long long* amax, int nsm, cudaStream_t st, TcDiag diag,
+                           TcOut lay) {
   using C = Cfg<S, BN>;
   if (nprob <= 0 || M <= 0 || N <= 0) return cudaSuccess;
-  if (RM && (ldo % 4 != 0 || ldo < ((N + 15) & ~15))) return cudaErrorInvalidValue;
+  if (RM && lay.mode == kOutRows && (ldo % 4 != 0 || ldo < ((N + 15) & ~15)))
+    return cudaErrorInvalidValue;
+  if (lay.mode != kOutRows &&
+      (!RM || lay.nbs < 1 || lay.nbt < 1 || (lay.mode == kOutYTile && lay.nvt < 1)))
+    return cudaErrorInvalidValue;
   auto k = tc_gemm_sliced<S, BN, OutT, TF, RM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   if (e != cudaSuccess) return e;
   const long long ntiles = (long long)nprob * ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int grid = (int)(ntiles < nsm ? ntiles : nsm);
   k<<<grid, 192, C::kSmem, st>>>(mA[0], mA[1], mB[0], mB[1], probs_dev, nprob, M, N, ldo, scale,
-                                 flag, amax, diag);
+                                 flag, amax, diag, lay);
   return cudaGetLastError();
 }
 
@@ -683,7 +695,7 @@ long long tc_default_wait_cycles() { return kWaitCycles; }
 #define LNO_TC_INST(S, BN, T, TF, RM)                                                        \
   template cudaError_t launch_tc_gemm<S, BN, T, TF, RM>(                                     \
       const CUtensorMap*, const CUtensorMap*, const TcProb*, int, int, int, int, double, int*, \
-      unsigned long long*, int, cudaStream_t, TcDiag);
+      unsigned long long*, int, cudaStream_t, TcDiag, TcOut);
 // W contractions (float32 row-major output): slices x tile width
 LNO_TC_INST(2, 256, float, false, true)
 LNO_TC_INST(2, 128, float, false, true)
