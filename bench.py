@@ -61,17 +61,13 @@ def peaks():
 
 
 # DRAM bytes (read + write) per tensor-core flop of the contraction kernel as
-# it is now, from one ncu capture per precision on a c1-sized group (filled in
-# from the capture named in the profiles folder; None = not captured since the
-# kernel last changed, and the line then reports traffic null).  The
+# it is now, from one ncu capture per precision on a c1-sized group; the
 # per-launch traffic scales with the launch's tensor flops at a fixed virtual
-# space.
-DRAM_BYTES_PER_TENSOR_FLOP = {
-    # tc_gemm_sliced<4,128,float,row-major>, nbas 368 nocc 8/6 naux 1200 group:
-    # 10.642 GB over 15 331 800 MMAs of 128x128x16
-    # (profiles/tc_gemm_sliced_bf16x10_c1shape.md)
-    "bf16x10": 10.642e9 / (15331800 * 128 * 128 * 16 * 2),
-}
+# space.  None is listed while the kernel has changed since its last capture
+# (profiles/tc_gemm_sliced_bf16x10_c1shape.md holds the last one, 1.3239e-3
+# B/flop, before the register-staged epilogue and the tiled Y/Z' stores), and
+# the bench line then reports traffic as null.
+DRAM_BYTES_PER_TENSOR_FLOP = {}
 
 # FP32 operations per restricted (abc) element in the float32 energy kernel
 # (an FMA counts 2): W 2, V 17 (same spin) / 9 (mixed), W (W + V) 2,
